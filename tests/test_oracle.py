@@ -1,0 +1,340 @@
+"""Pins of the FP64 oracle against facts fixed outside it.
+
+Each test names the passage of the paper it pins and the independent fact it
+uses: a library routine (numpy's FFT, dense solve), a closed form, an
+invariant, or a number printed in the paper (tests/golden/).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_rot(M, seed):
+    return synth.haar_rotations(M, seed)
+
+
+def _groups():
+    return synth.ctf_group_table([1.5, 2.5], pixel_A=2.8)
+
+
+# -- sample set and CTF ------------------------------------------------------
+
+def test_disc_sizes_match_row_count_fixture():
+    """eq. truncation: |K| against the integer row-count fixture."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "disc_counts.txt")) if not l.startswith("#")]
+    for N, cnt in ((int(a), int(b)) for a, b in rows):
+        K = O.disc(N)
+        assert K.shape[0] == cnt
+        assert np.all((K ** 2).sum(1) <= (N // 2) ** 2)
+        # symmetric: -k in K for every k (reading 1)
+        s = {tuple(k) for k in K}
+        assert all((-a, -b) in s for a, b in s)
+    assert O.disc(32, disc_mode=1).shape[0] == 795
+
+
+def test_wavelength_matches_paper_fig2():
+    """Fig. 2 caption: lambda = 2.51 pm, the 200 kV wavelength; 300 kV gives 1.9687 pm."""
+    kV, pm, tol = np.loadtxt(os.path.join(GOLD, "ctf_wavelength.txt"))
+    assert abs(O.electron_wavelength_A(kV) * 100 - pm) < tol
+    assert abs(O.electron_wavelength_A(300.0) * 100 - 1.9687) < 1e-3
+
+
+def test_ctf_special_values():
+    """CTF (Section 3.1): h(0) = -sin(A); first zero near 1/sqrt(lambda*df) (thin-lens
+    Scherzer relation, corrected for A); |h| <= 1; B-factor damps."""
+    g = (20000.0, 300.0, 2.0, 0.07, 2.8, 0.0)
+    assert O.ctf(0.0, g) == pytest.approx(-np.sin(0.07), abs=1e-15)
+    lam = O.electron_wavelength_A(300.0)
+    r0 = np.sqrt((1 - 0.07 / np.pi) / (lam * 20000.0))        # Cs term negligible here
+    r = np.linspace(0.5 * r0, 1.5 * r0, 20001)
+    h = O.ctf(r, g)
+    zero = r[np.nonzero(np.diff(np.sign(h)))[0][0]]
+    assert abs(zero - r0) / r0 < 5e-3
+    rr = np.linspace(0, 0.2, 1000)
+    assert np.all(np.abs(O.ctf(rr, g)) <= 1 + 1e-15)
+    gB = (20000.0, 300.0, 2.0, 0.07, 2.8, 100.0)
+    assert O.ctf(0.1, gB) == pytest.approx(O.ctf(0.1, g) * np.exp(-100 * 0.01 / 4), rel=1e-12)
+
+
+# -- forward projector against numpy's FFT (special rotations) ------------------
+
+def _centered_fft2(img, K):
+    """Centred DFT (Section 2.2) read off numpy's FFT: sum_i x_i e^{-2pi i k (i-N/2)/N} = (-1)^k fft[k]."""
+    N = img.shape[-1]
+    F = np.fft.fft2(img)                      # axes (-2, -1) = (k on axis0, k on axis1)
+    sgn = (-1.0) ** (K[:, 0] + K[:, 1])
+    return F[..., K[:, 0] % N, K[:, 1] % N] * sgn
+
+
+def test_forward_identity_rotation_is_dft_of_line_sum():
+    """eq. forward-projector with R = I: A(V)(k) = h * 2D DFT of sum_{n3} V (numpy fft2)."""
+    N = 8
+    rng = np.random.default_rng(5)
+    V = rng.standard_normal((N, N, N))
+    K = O.disc(N)
+    R = np.eye(3)[None]
+    h = rng.uniform(0.5, 1.5, (1, K.shape[0]))
+    A = O.forward(V, R, h, K)[0]
+    line = V.sum(axis=0)                      # [i2][i1]; k1 pairs with n1 (axis 1)
+    ref = _centered_fft2(line.T, K) * h[0]    # transpose so axis0 = n1
+    np.testing.assert_allclose(A, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_forward_quarter_turn_projects_along_x():
+    """R with rows (0,0,1), (0,1,0), (-1,0,0): xi = (0, w2, w1), so A(V) is the DFT of the
+    line sum along n1 with k1 <-> n3 and k2 <-> n2.  Using R instead of R^T flips k1."""
+    N = 8
+    rng = np.random.default_rng(6)
+    V = rng.standard_normal((N, N, N))
+    K = O.disc(N)
+    R = np.array([[[0.0, 0, 1], [0, 1, 0], [-1, 0, 0]]])
+    h = np.ones((1, K.shape[0]))
+    A = O.forward(V, R, h, K)[0]
+    line = V.sum(axis=2)                      # [n3][n2]
+    ref = _centered_fft2(line, K)             # axis0 = n3 <-> k1, axis1 = n2 <-> k2
+    np.testing.assert_allclose(A, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+    bad = O.forward(V, R.transpose(0, 2, 1), h, K)[0]
+    assert np.abs(bad - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+# -- adjoint, kernel, Toeplitz ----------------------------------------------------
+
+@pytest.mark.parametrize("N,M", [(6, 5), (8, 7)])
+def test_adjoint_identity(N, M):
+    """Definition of A* (Section 3.2): <A V, g> = <V, A* g> for random V, g."""
+    rng = np.random.default_rng(N * 100 + M)
+    K = O.disc(N)
+    R = _rand_rot(M, 7)
+    gid = rng.integers(0, 2, M)
+    h = O.ctf_weights(N, K, _groups(), gid)
+    V = rng.standard_normal((N,) * 3) + 1j * rng.standard_normal((N,) * 3)
+    g = rng.standard_normal((M, K.shape[0])) + 1j * rng.standard_normal((M, K.shape[0]))
+    lhs = np.vdot(g, O.forward(V, R, h, K))           # <A V, g> = sum A(V) conj(g)
+    rhs = np.vdot(O.adjoint(g, R, h, K, N), V)        # <V, A* g> = sum V conj(A* g)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_kernel_closed_form_at_origin_and_symmetry():
+    """eq. kernel at n = 0 is sum_m sum_k h^2; Ker(-n) = conj Ker(n) (Section 3.4); under the
+    symmetric disc Ker is real.  The DFT-range disc (disc_mode 1) is not real."""
+    N, M = 8, 6
+    rng = np.random.default_rng(1)
+    K = O.disc(N)
+    R = _rand_rot(M, 3)
+    h = O.ctf_weights(N, K, _groups(), rng.integers(0, 2, M))
+    Ker = O.kernel(R, h, K, N)
+    assert Ker[N, N, N].real == pytest.approx((h * h).sum(), rel=1e-13)
+    flip = Ker[:0:-1, :0:-1, :0:-1]           # n -> -n for n in (-N, N)
+    np.testing.assert_allclose(Ker[1:, 1:, 1:], np.conj(flip), atol=1e-10 * abs(Ker).max())
+    assert np.abs(Ker.imag).max() < 1e-10 * abs(Ker).max()
+    K1 = O.disc(N, 1)
+    Ker1 = O.kernel(R, O.ctf_weights(N, K1, _groups(), rng.integers(0, 2, M)), K1, N)
+    assert np.abs(Ker1.imag).max() > 1e-6 * abs(Ker1).max()
+
+
+def test_kernel_at_matches_full_kernel():
+    """kernel_at (per-image factorisation) equals the chunked direct sum of eq. kernel."""
+    N, M = 8, 9
+    K = O.disc(N)
+    R = _rand_rot(M, 4)
+    h = O.ctf_weights(N, K, _groups(), np.arange(M) % 2)
+    Ker = O.kernel(R, h, K, N)
+    rng = np.random.default_rng(2)
+    nv = rng.integers(-N, N, (20, 3))
+    got = O.kernel_at(R, h, K, N, nv)
+    ref = Ker[nv[:, 2] + N, nv[:, 1] + N, nv[:, 0] + N]
+    np.testing.assert_allclose(got, ref, atol=1e-11 * abs(Ker).max())
+
+
+def test_octahedral_invariance_and_axis_permutation():
+    """eq. kernel: premultiplying every R_m by a quarter turn about the beam axis permutes the
+    disc lattice, so Ker is unchanged; R_m P^T (P a permutation) permutes Ker's axes."""
+    N, M = 8, 5
+    K = O.disc(N)
+    R = _rand_rot(M, 8)
+    h = O.ctf_weights(N, K, _groups(), np.arange(M) % 2)
+    Ker = O.kernel(R, h, K, N)
+    Rz = np.array([[0.0, -1, 0], [1, 0, 0], [0, 0, 1]])
+    Ker_z = O.kernel(np.einsum("ij,mjk->mik", Rz, R), h, K, N)
+    np.testing.assert_allclose(Ker_z, Ker, atol=1e-10 * abs(Ker).max())
+    # P maps (x, y, z) -> (y, z, x)
+    P = np.array([[0.0, 1, 0], [0, 0, 1], [1, 0, 0]])
+    Ker_p = O.kernel(np.einsum("mij,kj->mik", R, P), h, K, N)
+    # Ker_p(n) = Ker(P^T n); P^T n = (n3, n1, n2) as (x, y, z)
+    n = np.arange(-N, N)
+    n1, n2, n3 = np.meshgrid(n, n, n, indexing="ij")          # axes: (x, y, z)
+    ref = Ker[n2 + N, n1 + N, n3 + N]     # Ker stored [z][y][x] at (x,y,z) = (n3, n1, n2)
+    got = Ker_p.transpose(2, 1, 0)        # to (x, y, z) axes
+    np.testing.assert_allclose(got, ref, atol=1e-10 * abs(Ker).max())
+
+
+def test_toeplitz_identity():
+    """eq. toeplitz / eq. property: A*(A V) equals the convolution of Ker with V."""
+    N, M = 6, 7
+    rng = np.random.default_rng(9)
+    K = O.disc(N)
+    R = _rand_rot(M, 10)
+    h = O.ctf_weights(N, K, _groups(), rng.integers(0, 2, M))
+    V = rng.standard_normal((N,) * 3)
+    lhs = O.adjoint(O.forward(V, R, h, K), R, h, K, N)
+    rhs = O.toeplitz_direct(O.kernel(R, h, K, N), V)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-11 * abs(rhs).max())
+
+
+def test_circulant_embedding_equals_direct_toeplitz():
+    """eq. embedding_circulant with the 0-based map (reading 2): the FFT product on the 2N grid,
+    cropped, equals the O(N^6) Toeplitz sum; the lag +-N plane never reaches the crop."""
+    N, M = 8, 6
+    rng = np.random.default_rng(11)
+    K = O.disc(N)
+    R = _rand_rot(M, 12)
+    h = O.ctf_weights(N, K, _groups(), rng.integers(0, 2, M))
+    Ker = O.kernel(R, h, K, N)
+    V = rng.standard_normal((N,) * 3)
+    ref = O.toeplitz_direct(Ker, V)
+    got = O.toeplitz_apply(O.khat(Ker), V)
+    np.testing.assert_allclose(got, ref, atol=1e-11 * abs(ref).max())
+    # the lag -N planes never reach the crop: holding Ker there, or junk, changes nothing
+    got_ker = O.toeplitz_apply(O.khat(Ker, lag_n_planes="ker"), V)
+    np.testing.assert_allclose(got_ker, ref, atol=1e-11 * abs(ref).max())
+    Ker2 = Ker.copy()
+    Ker2[0], Ker2[:, 0], Ker2[:, :, 0] = 123.0, -7.0, 5.0      # the n_j = -N planes
+    got2 = O.toeplitz_apply(O.khat(Ker2, lag_n_planes="ker"), V)
+    np.testing.assert_allclose(got2, ref, atol=1e-11 * abs(ref).max())
+
+
+def test_khat_real_and_half_spectrum():
+    """Under reading 1 Ker(-n) = Ker(n) is real, so K-hat (eq. circ1) is real and K-hat(-j) =
+    K-hat(j); the half spectrum j1 <= N holds all of it.  K-hat is not even per axis."""
+    N, M = 8, 5
+    K = O.disc(N)
+    R = _rand_rot(M, 13)
+    h = O.ctf_weights(N, K, _groups(), np.arange(M) % 2)
+    Ker = O.kernel(R, h, K, N)
+    Kh = O.khat(Ker)
+    assert np.abs(Kh.imag).max() < 1e-9 * abs(Kh).max()
+    j = np.arange(2 * N)
+    neg = (-j) % (2 * N)
+    np.testing.assert_allclose(Kh[np.ix_(neg, neg, neg)], Kh, atol=1e-9 * abs(Kh).max())
+    H = O.khat_half(Ker)
+    assert H.shape == (2 * N, 2 * N, N + 1)
+    full = np.where((j <= N)[None, None, :], H[:, :, np.minimum(j, N)],
+                    H[np.ix_(neg, neg, np.minimum(neg, N))])
+    np.testing.assert_allclose(full, Kh.real, atol=1e-9 * abs(Kh).max())
+    assert np.abs(Kh.real - Kh.real[:, :, neg]).max() > 1e-6 * abs(Kh).max()
+
+
+# -- image DFT, shifts, analytic projections ------------------------------------------
+
+def test_image_dft_against_numpy_and_integer_shift():
+    """Step 1 / eq. measurement: the centred DFT equals numpy's fft2 read at the disc; an image
+    rolled by an integer shift s and given s returns the unshifted samples (reading 4)."""
+    N, M = 16, 3
+    rng = np.random.default_rng(14)
+    I = rng.standard_normal((M, N, N))
+    K = O.disc(N)
+    b = O.image_dft(I, K)
+    ref = np.stack([_centered_fft2(I[m].T, K) for m in range(M)])   # axis0 = n1
+    np.testing.assert_allclose(b, ref, atol=1e-11 * abs(ref).max())
+    s = np.array([[2, -3], [0, 1], [-1, 0]], float)
+    Is = np.stack([np.roll(I[m], (int(s[m, 1]), int(s[m, 0])), axis=(0, 1)) for m in range(M)])
+    np.testing.assert_allclose(O.image_dft(Is, K, s), b, atol=1e-10 * abs(b).max())
+
+
+def test_analytic_projection_matches_forward_projector():
+    """Fourier slice theorem (eq. continuous_fps and its discrete form, Section 3.1): the DFT of
+    the analytic projection of a band-limited blob phantom equals A(V) of the sampled phantom.
+    Pins the rotation convention shared with the data generator."""
+    N, M = 32, 4
+    bl = synth.Blobs(np.array([[2.0, -3.0, 1.0], [-4.0, 1.0, 3.0]]), np.array([2.0, 2.2]),
+                     np.array([1.0, 0.7]))
+    V = synth.blob_volume(bl, N)
+    R = _rand_rot(M, 15)
+    img = synth.project_blobs(bl, R, N, dtype=np.float64)
+    K = O.disc(N)
+    b = O.image_dft(img, K)
+    A = O.forward(V, R, np.ones((M, K.shape[0])), K)
+    assert np.abs(b - A).max() < 1e-6 * np.abs(A).max()
+
+
+def test_backprojection_of_real_images_is_real():
+    """Reading 1/7: with the symmetric disc A*b of real, shifted images is real."""
+    N, M = 8, 4
+    rng = np.random.default_rng(16)
+    I = rng.standard_normal((M, N, N))
+    K = O.disc(N)
+    R = _rand_rot(M, 17)
+    h = O.ctf_weights(N, K, _groups(), rng.integers(0, 2, M))
+    s = rng.uniform(-2, 2, (M, 2))
+    full = O.adjoint(O.image_dft(I, K, s), R, h, K, N)
+    assert np.abs(full.imag).max() < 1e-10 * np.abs(full.real).max()
+    nv = rng.integers(-N // 2, N // 2, (6, 3))
+    at = O.backproject_at(I, s, R, h, K, nv)
+    np.testing.assert_allclose(at, full[nv[:, 2] + N // 2, nv[:, 1] + N // 2, nv[:, 0] + N // 2],
+                               atol=1e-10 * abs(full).max())
+
+
+# -- CG ------------------------------------------------------------------------------------
+
+def test_cg_identity_operator_one_step():
+    """CG (Section 3.3) on lam_eff * I (no images) converges in one iteration to rhs / lam_eff."""
+    rng = np.random.default_rng(18)
+    rhs = rng.standard_normal((4, 4, 4))
+    x, hist, it = O.cg(lambda v: 2.5 * v, rhs, 10, rel_tol=1e-14)
+    assert it == 1
+    np.testing.assert_allclose(x, rhs / 2.5, rtol=1e-14)
+
+
+def test_cg_matches_dense_solve_of_explicit_toeplitz_system():
+    """CG (Section 3.3) on (Ker * . + lam I) equals numpy's dense solve of the explicit
+    N^3 x N^3 Toeplitz matrix (eq. toep3) at N = 4."""
+    N, M = 4, 6
+    K = O.disc(N)
+    R = _rand_rot(M, 19)
+    h = O.ctf_weights(N, K, _groups(), np.arange(M) % 2)
+    Ker = O.kernel(R, h, K, N).real
+    lam = O.lambda_eff(1e-2, 0, Ker[N, N, N])
+    n = np.stack(np.meshgrid(*(np.arange(N),) * 3, indexing="ij"), -1).reshape(-1, 3)   # (z,y,x)
+    d = n[:, None, :] - n[None, :, :] + N
+    T = Ker[d[..., 0], d[..., 1], d[..., 2]] + lam * np.eye(N ** 3)
+    rng = np.random.default_rng(20)
+    rhs = rng.standard_normal((N,) * 3)
+    ref = np.linalg.solve(T, rhs.reshape(-1)).reshape((N,) * 3)
+    Kh = O.khat(Ker)
+    x, hist, it = O.cg(lambda v: O.toeplitz_apply(Kh, v, lam).real, rhs, 400, rel_tol=1e-13)
+    np.testing.assert_allclose(x, ref, atol=1e-9 * abs(ref).max())
+    # A-norm of the error decreases monotonically along the iterates (CG optimality)
+    errs = []
+    O.cg(lambda v: O.toeplitz_apply(Kh, v, lam).real, rhs, 30,
+         callback=lambda i, xx, rr: errs.append(float((xx - ref).ravel() @ T @ (xx - ref).ravel())))
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(errs, errs[1:]))
+
+
+def test_cg_recovers_blob_phantom_from_dense_noiseless_views():
+    """FIRM steps 2-4 (Section 3.4) on noiseless data b = A(V0) from many uniform views recover V0.
+
+    CG from zero stays in the range of A*; V0 = (A*A) V_blob lies there and is recovered to
+    1e-6.  The raw blob also carries Fourier content outside the ball |xi| <= pi that A does
+    not see (Section 3.3: ill-conditioning), so it is only approached slowly."""
+    N, M = 8, 120
+    bl = synth.phantom_blobs(3, N, 21, sigma_range=(1.0, 1.5))
+    Vb = synth.blob_volume(bl, N)
+    K = O.disc(N)
+    R = synth.haar_rotations(M, 22)
+    h = np.ones((M, K.shape[0]))
+    Kh = O.khat(O.kernel(R, h, K, N))
+    op = lambda v: O.toeplitz_apply(Kh, v).real
+    V0 = op(Vb)
+    V0 /= np.abs(V0).max()
+    rhs = O.adjoint(O.forward(V0, R, h, K), R, h, K, N).real
+    x, hist, it = O.cg(op, rhs, 100)
+    assert np.linalg.norm(x - V0) / np.linalg.norm(V0) <= 1e-6
+    rhs_b = O.adjoint(O.forward(Vb, R, h, K), R, h, K, N).real
+    xb, _, _ = O.cg(op, rhs_b, 500)
+    assert np.linalg.norm(xb - Vb) / np.linalg.norm(Vb) <= 5e-5
