@@ -1,0 +1,162 @@
+/*
+ * firm.h -- C ABI of the GB300 FIRM hot path.
+ *
+ * FIRM (Wang, Shkolnisky & Singer, "A Fourier-based Approach for Iterative 3D
+ * Reconstruction from Cryo-EM Images") reconstructs a volume V from M projection
+ * images with known rotations R_m, shifts s_m and CTFs h_m by solving
+ *     (A*A + lam_eff I) V = A*b                                  (Section 3.3)
+ * with conjugate gradients, where A*A is applied as a convolution with the kernel
+ * Ker through a 2N circulant embedding (Section 3.2, eq. property,
+ * eq. embedding_circulant) and Ker and A*b are computed once by type-1 NUFFT
+ * (Section 3.4, steps 2-3; eq. kernel, eq. backprojection).
+ *
+ * Conventions (shared by every entry point):
+ *   - A volume is N^3 float32, row-major [i3][i2][i1] (i1 = x fastest), voxel index
+ *     i_j <-> centred coordinate n_j = i_j - N/2 (Section 3.1).
+ *   - Images are M x N x N, [m][i2][i1], float32 or bfloat16 (firm_params.img_dtype).
+ *   - R is M x 9 float64, each rotation row-major.  The slice of image m samples
+ *     the points xi = R_m^T (2 pi k1 / N, 2 pi k2 / N, 0) for |k| <= N/2
+ *     (eq. forward-projector, eq. truncation: the symmetric disc).
+ *   - shifts is M x 2 float64 (x, y) in pixels; the samples of image m are
+ *     multiplied by exp(+2 pi i <k, s_m> / N) before back-projection.
+ *   - group is M int32 defocus-group indices into the plan's CTF table.
+ *   - K-hat (the eigenvalues of the circulant, eq. circ1) is real; it is stored as
+ *     the half spectrum 2N x 2N x (N+1) float32, [j3][j2][j1] with j1 in [0, N].
+ *   - Ker is stored the same way: [n3+N][n2+N][n1], n1 in [0, N], n2, n3 in [-N, N)
+ *     (Ker(-n) = Ker(n), so the half holds every value).
+ *
+ * Pointers: every array argument may be host or device memory (the library asks
+ * the CUDA runtime which).  Host inputs are copied into the plan's workspace; host
+ * outputs are copied back before the call returns.  Device arrays are read or
+ * written in stream order on the plan's stream; the call returns without waiting
+ * unless a host output, a host residual history or a relative tolerance needs it.
+ *
+ * Ownership: the caller owns every array it passes, including the plan's
+ * workspace (firm_workspace_size / firm_plan); the library allocates no device
+ * memory of its own.  Buffers must not be freed while work queued on the stream may
+ * still use them.
+ *
+ * Errors: every call returns a firm_status; nothing aborts or throws.  A call that
+ * fails leaves its outputs unspecified; the plan stays usable unless the status is
+ * FIRM_ECUDA (a CUDA error: the context may be lost).
+ */
+#ifndef FIRM_H
+#define FIRM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FIRM_OK = 0,
+    FIRM_EINVAL = 1,      /* bad argument: size, null pointer, unsupported option */
+    FIRM_ENOMEM = 2,      /* workspace smaller than firm_workspace_size() */
+    FIRM_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    FIRM_ENOTCONV = 4,    /* CG reached max_iter above rel_tol */
+    FIRM_EBREAKDOWN = 5,  /* CG breakdown: <p, Ap> <= 0 or a non-finite scalar */
+    FIRM_ETIMEOUT = 6,    /* a bounded device wait gave up (never expected) */
+    FIRM_ESTATE = 7       /* call order: e.g. firm_cg_solve before firm_kernel */
+} firm_status;
+
+enum { FIRM_IMG_F32 = 0, FIRM_IMG_BF16 = 1 };
+enum { FIRM_LAMBDA_RELATIVE = 0, FIRM_LAMBDA_ABSOLUTE = 1 };
+
+/* One defocus group of the CTF of Section 3.1, read as
+ *   h(r) = -sin(chi(r) + amp_contrast) * exp(-bfactor_A2 * r^2 / 4),
+ *   chi(r) = pi * lambda * defocus_A * r^2 - (pi/2) * Cs * lambda^3 * r^4,
+ * r = |k| / (N * pixel_A) in 1/Angstrom, lambda the relativistic wavelength at kV,
+ * Cs = Cs_mm * 1e7 Angstrom.  amp_contrast enters as a phase in radians. */
+typedef struct {
+    double defocus_A, kV, Cs_mm, amp_contrast, pixel_A, bfactor_A2;
+} firm_ctf_group;
+
+typedef struct {
+    int N;            /* volume edge: even, 8 <= N <= 256 (2N and 4N must be FFT sizes) */
+    int M;            /* largest image count any call on the plan will pass */
+    int n_groups;     /* defocus groups in the CTF table; 0 means no CTF (h = 1) */
+    int W;            /* Kaiser-Bessel window width in fine-grid cells: 6, 7 or 8 */
+    double sigma;     /* NUFFT oversampling; only 2 is supported */
+    double lambda;    /* Tikhonov weight */
+    int lambda_mode;  /* FIRM_LAMBDA_RELATIVE: lam_eff = lambda * Ker(0); ABSOLUTE: lambda */
+    int disc_mode;    /* 0: symmetric disc |k| <= N/2 (the only mode of the CUDA path) */
+    int img_dtype;    /* FIRM_IMG_F32 or FIRM_IMG_BF16 */
+    int flags;        /* reserved, must be 0 */
+} firm_params;
+
+typedef struct firm_plan_s* firm_plan_t;
+
+/* Bytes of device workspace a plan with these parameters needs. */
+int firm_workspace_size(const firm_params* p, size_t* bytes);
+
+/* Create a plan: validates p, copies the CTF table (n_groups entries; may be NULL
+ * when n_groups == 0), precomputes the Kaiser-Bessel window polynomials, the
+ * deconvolution factors and the FFT tables, and carves `workspace` (device memory,
+ * at least firm_workspace_size bytes, 256-byte aligned) into its buffers.  stream is
+ * a cudaStream_t (NULL = legacy default stream).  On success *out owns no device
+ * memory; firm_destroy releases its host state. */
+int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* groups,
+              void* workspace, size_t workspace_bytes, void* stream);
+
+/* FIRM step 3 (Section 3.4; eq. kernel, eq. embedding_circulant, eq. circ1).
+ * Spreads the CTF^2-weighted slice samples of M <= p.M images onto the 4N^3 fine
+ * grid, transforms and deconvolves it to Ker on [-N, N)^3, embeds Ker in the 2N^3
+ * circulant and transforms it to K-hat, which the plan keeps for firm_cg_solve and
+ * firm_toeplitz_apply.  khat_out (nullable) receives a copy of K-hat (half
+ * spectrum, see above).  Also fixes lam_eff (firm_lambda_eff). */
+int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, float* khat_out);
+
+/* FIRM steps 1-2 (Section 3.4; eq. measurement, eq. backprojection).  Takes the
+ * centred 2D DFT of each image on the disc, applies the shift phase and h_m, spreads
+ * the samples onto the 2N^3 fine grid, transforms and deconvolves to A*b on N^3.
+ * The plan keeps A*b; rhs_out (nullable) receives a copy (N^3 float32). */
+int firm_backproject(firm_plan_t plan, int M, const void* images, const double* shifts,
+                     const double* R, const int32_t* group, float* rhs_out);
+
+/* FIRM step 4 (Section 3.3): conjugate gradients on (A*A + lam_eff I) x = rhs from
+ * x = 0, with FP64 step lengths and residual recurrence.  rhs may be NULL (use the
+ * A*b kept by firm_backproject).  Runs max_iter iterations, or stops once the
+ * recurrence residual ||r_k|| <= rel_tol ||rhs|| (rel_tol > 0; the check reads one
+ * flag per batch of iterations).  x receives the iterate (N^3).  resid_hist
+ * (nullable, max_iter+1 doubles) receives ||r_k|| for k = 0..iters; *iters_out
+ * (nullable) the iterations run.  Returns FIRM_ENOTCONV if rel_tol > 0 was not met,
+ * FIRM_EBREAKDOWN on <p, Ap> <= 0 or a non-finite scalar (x then holds the last
+ * good iterate). */
+int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, double rel_tol,
+                  double* resid_hist, int* iters_out);
+
+/* One application of the regularised normal operator, y = Ker * x + lam_eff x
+ * (eq. property through the circulant embedding of Section 3.2), using the K-hat of
+ * the last firm_kernel.  x and y are N^3 and must not overlap. */
+int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y);
+
+/* lam_eff of the last firm_kernel (Tikhonov weight actually added to A*A). */
+int firm_lambda_eff(firm_plan_t plan, double* out);
+
+/* Copies of intermediate results kept by the plan (for verification):
+ *   FIRM_OUT_KER   Ker half box, 2N x 2N x (N+1) float32 (eq. kernel)
+ *   FIRM_OUT_KHAT  K-hat half spectrum, 2N x 2N x (N+1) float32 (eq. circ1)
+ *   FIRM_OUT_RHS   A*b, N^3 float32 (eq. backprojection)
+ *   FIRM_OUT_SAMPLES  h_m b_m(k) on the half disc, M x |H| complex float32, with the
+ *                  k = 0 sample halved (the symmetric completion doubles it back).
+ *                  |H| = (|K| + 1) / 2, ordered by k1 = 0..N/2 then k2 ascending,
+ *                  starting (0,0), (0,1), ... (0,N/2), (1,-..), ... */
+enum { FIRM_OUT_KER = 0, FIRM_OUT_KHAT = 1, FIRM_OUT_RHS = 2, FIRM_OUT_SAMPLES = 3 };
+int firm_copy_out(firm_plan_t plan, int which, void* dst);
+
+/* Timing of the last call of each stage (milliseconds of device time between CUDA
+ * events on the plan's stream): index 0 binning, 1 spreading, 2 fine-grid FFT +
+ * deconvolution, 3 circulant K-hat, 4 image DFT, 5 CG total, 6 CG iterations run.
+ * Filled only when timing was enabled with firm_set_timing(plan, 1). */
+int firm_set_timing(firm_plan_t plan, int on);
+int firm_stage_times(firm_plan_t plan, double* out7);
+
+void firm_destroy(firm_plan_t plan);
+const char* firm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIRM_H */

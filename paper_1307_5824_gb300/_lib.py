@@ -1,0 +1,181 @@
+"""ctypes binding of include/firm.h: same names, argument marshalling only.
+
+Arrays may be torch tensors (CPU or CUDA) or numpy arrays; the library decides
+from the pointer whether memory is host or device.  Every step of the
+computation runs inside libfirm.so; nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfirm.so")
+
+FIRM_OK, FIRM_EINVAL, FIRM_ENOMEM, FIRM_ECUDA, FIRM_ENOTCONV, FIRM_EBREAKDOWN, FIRM_ETIMEOUT, FIRM_ESTATE = range(8)
+FIRM_IMG_F32, FIRM_IMG_BF16 = 0, 1
+FIRM_LAMBDA_RELATIVE, FIRM_LAMBDA_ABSOLUTE = 0, 1
+FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES = 0, 1, 2, 3
+
+EXPORTED = [
+    "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_cg_solve",
+    "firm_toeplitz_apply", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
+    "firm_stage_times", "firm_destroy", "firm_strerror",
+]
+
+
+class firm_ctf_group(ctypes.Structure):
+    _fields_ = [("defocus_A", ctypes.c_double), ("kV", ctypes.c_double), ("Cs_mm", ctypes.c_double),
+                ("amp_contrast", ctypes.c_double), ("pixel_A", ctypes.c_double),
+                ("bfactor_A2", ctypes.c_double)]
+
+
+class firm_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("n_groups", ctypes.c_int), ("W", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("lambda_", ctypes.c_double), ("lambda_mode", ctypes.c_int),
+                ("disc_mode", ctypes.c_int), ("img_dtype", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class FirmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} (status {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfirm.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.firm_workspace_size.argtypes = [ctypes.POINTER(firm_params), ctypes.POINTER(ctypes.c_size_t)]
+    L.firm_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(firm_params), ctypes.POINTER(firm_ctf_group),
+                            vp, ctypes.c_size_t, vp]
+    L.firm_kernel.argtypes = [vp, i, vp, vp, vp]
+    L.firm_backproject.argtypes = [vp, i, vp, vp, vp, vp, vp]
+    L.firm_cg_solve.argtypes = [vp, vp, vp, i, d, vp, ctypes.POINTER(i)]
+    L.firm_toeplitz_apply.argtypes = [vp, vp, vp]
+    L.firm_lambda_eff.argtypes = [vp, ctypes.POINTER(d)]
+    L.firm_copy_out.argtypes = [vp, i, vp]
+    L.firm_set_timing.argtypes = [vp, i]
+    L.firm_stage_times.argtypes = [vp, ctypes.POINTER(d)]
+    L.firm_destroy.argtypes = [vp]
+    L.firm_destroy.restype = None
+    L.firm_strerror.argtypes = [i]
+    L.firm_strerror.restype = ctypes.c_char_p
+    for name in EXPORTED[:-2]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return lib().firm_strerror(int(code)).decode()
+
+
+def _ptr(a):
+    """Raw address of a torch tensor / numpy array (None -> NULL).  Must be contiguous."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(code: int, what: str):
+    if code != FIRM_OK:
+        raise FirmError(code, what)
+
+
+def make_params(N, M, n_groups=0, W=7, sigma=2.0, lam=0.0, lambda_mode=FIRM_LAMBDA_RELATIVE, disc_mode=0,
+                img_dtype=FIRM_IMG_F32, flags=0) -> firm_params:
+    return firm_params(N, M, n_groups, W, sigma, lam, lambda_mode, disc_mode, img_dtype, flags)
+
+
+def make_groups(table) -> ctypes.Array | None:
+    """(G, 6) table (defocus_A, kV, Cs_mm, amp_contrast, pixel_A, bfactor_A2) -> firm_ctf_group[G]."""
+    table = np.asarray(table, float).reshape(-1, 6)
+    if table.shape[0] == 0:
+        return None
+    arr = (firm_ctf_group * table.shape[0])()
+    for g, row in enumerate(table):
+        arr[g] = firm_ctf_group(*[float(v) for v in row])
+    return arr
+
+
+def firm_workspace_size(params: firm_params) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().firm_workspace_size(ctypes.byref(params), ctypes.byref(n)), "firm_workspace_size")
+    return int(n.value)
+
+
+def firm_plan(params: firm_params, groups, workspace, workspace_bytes: int, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    g = ctypes.cast(groups, ctypes.POINTER(firm_ctf_group)) if groups is not None else None
+    _check(lib().firm_plan(ctypes.byref(h), ctypes.byref(params), g, _ptr(workspace), workspace_bytes, stream),
+           "firm_plan")
+    return h
+
+
+def firm_kernel(plan, M: int, R, group=None, khat_out=None):
+    _check(lib().firm_kernel(plan, M, _ptr(R), _ptr(group), _ptr(khat_out)), "firm_kernel")
+
+
+def firm_backproject(plan, M: int, images, shifts, R, group=None, rhs_out=None):
+    _check(lib().firm_backproject(plan, M, _ptr(images), _ptr(shifts), _ptr(R), _ptr(group), _ptr(rhs_out)),
+           "firm_backproject")
+
+
+def firm_cg_solve(plan, rhs, x, max_iter: int, rel_tol: float = 0.0, resid_hist=None, allow=()):
+    """Returns (status, iterations).  Raises unless the status is OK or listed in `allow`."""
+    it = ctypes.c_int(0)
+    st = lib().firm_cg_solve(plan, _ptr(rhs), _ptr(x), int(max_iter), float(rel_tol), _ptr(resid_hist),
+                             ctypes.byref(it))
+    if st != FIRM_OK and st not in allow:
+        raise FirmError(st, "firm_cg_solve")
+    return st, int(it.value)
+
+
+def firm_toeplitz_apply(plan, x, y):
+    _check(lib().firm_toeplitz_apply(plan, _ptr(x), _ptr(y)), "firm_toeplitz_apply")
+
+
+def firm_lambda_eff(plan) -> float:
+    v = ctypes.c_double(0)
+    _check(lib().firm_lambda_eff(plan, ctypes.byref(v)), "firm_lambda_eff")
+    return float(v.value)
+
+
+def firm_copy_out(plan, which: int, dst):
+    _check(lib().firm_copy_out(plan, int(which), _ptr(dst)), "firm_copy_out")
+
+
+def firm_set_timing(plan, on: bool):
+    _check(lib().firm_set_timing(plan, 1 if on else 0), "firm_set_timing")
+
+
+def firm_stage_times(plan):
+    out = (ctypes.c_double * 7)()
+    _check(lib().firm_stage_times(plan, out), "firm_stage_times")
+    return list(out)
+
+
+def firm_destroy(plan):
+    if plan:
+        lib().firm_destroy(plan)

@@ -1,0 +1,585 @@
+// api.cu -- the C ABI of include/firm.h: plan, workspace layout, host tables, staging
+// of host inputs, and the FIRM steps (Section 3.4) in stream order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "firm_internal.h"
+
+namespace firm {
+
+static const double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Host tables
+// ---------------------------------------------------------------------------
+
+// Modified Bessel function I0 by its defining power series sum (x^2/4)^k / (k!)^2.
+static double bessel_i0(double x) {
+    const double q = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+static double kb_beta(int W, double sigma) {
+    // Beatty, Nishimura & Pauly (2005): beta = pi sqrt((W/sigma)^2 (sigma - 1/2)^2 - 0.8)
+    const double a = (double)W / sigma * (sigma - 0.5);
+    return kPi * std::sqrt(a * a - 0.8);
+}
+
+static double kb_phi(double t, int W, double beta, double norm) {
+    const double s = 2.0 * t / W;
+    if (std::fabs(s) > 1.0) return 0.0;
+    return bessel_i0(beta * std::sqrt(1.0 - s * s)) / norm;
+}
+
+// Chebyshev interpolation of each tap's weight phi(u + l - W/2), u = (z+1)/2, on
+// kKbDeg+1 Chebyshev nodes, converted to monomials in z (Horner on the device).
+void kb_build(int W, double sigma, KbPoly& poly, double* beta_out) {
+    const double beta = kb_beta(W, sigma);
+    const double norm = bessel_i0(beta);
+    constexpr int D = kKbDeg;
+    std::memset(&poly, 0, sizeof(poly));
+    for (int l = 0; l < W; ++l) {
+        double f[D + 1], cheb[D + 1];
+        for (int j = 0; j <= D; ++j) {
+            const double z = std::cos(kPi * (j + 0.5) / (D + 1));
+            f[j] = kb_phi(0.5 * (z + 1.0) + l - 0.5 * W, W, beta, norm);
+        }
+        for (int k = 0; k <= D; ++k) {
+            double s = 0.0;
+            for (int j = 0; j <= D; ++j) s += f[j] * std::cos(kPi * k * (j + 0.5) / (D + 1));
+            cheb[k] = (k == 0 ? 1.0 : 2.0) * s / (D + 1);
+        }
+        // T_k -> monomials: T_0 = 1, T_1 = z, T_{k+1} = 2 z T_k - T_{k-1}
+        double Tm1[D + 1] = {0}, T0[D + 1] = {0}, T1[D + 1] = {0}, mono[D + 1] = {0};
+        T0[0] = 1.0;
+        for (int k = 0; k <= D; ++k) {
+            const double* Tk = (k == 0) ? T0 : T1;
+            for (int j = 0; j <= D; ++j) mono[j] += cheb[k] * Tk[j];
+            if (k == 0) {
+                std::memset(T1, 0, sizeof(T1));
+                T1[1] = 1.0;
+                std::memcpy(Tm1, T0, sizeof(T0));
+            } else {
+                double Tn[D + 1] = {0};
+                for (int j = 0; j < D; ++j) Tn[j + 1] += 2.0 * T1[j];
+                for (int j = 0; j <= D; ++j) Tn[j] -= Tm1[j];
+                std::memcpy(Tm1, T1, sizeof(T1));
+                std::memcpy(T1, Tn, sizeof(Tn));
+            }
+        }
+        for (int j = 0; j <= D; ++j) poly.c[l][j] = (float)mono[j];
+    }
+    if (beta_out) *beta_out = beta;
+}
+
+// Fourier transform of the normalised window, int phi(t) exp(-2 pi i u t) dt
+//   = W sinh(sqrt(beta^2 - (pi W u)^2)) / sqrt(beta^2 - (pi W u)^2) / I0(beta).
+double kb_phihat(double u, int W, double beta) {
+    const double a = beta * beta - (kPi * W * u) * (kPi * W * u);
+    double v;
+    if (a > 1e-12) { const double s = std::sqrt(a); v = std::sinh(s) / s; }
+    else if (a < -1e-12) { const double s = std::sqrt(-a); v = std::sin(s) / s; }
+    else v = 1.0;
+    return W * v / bessel_i0(beta);
+}
+
+std::vector<int32_t> half_disc(int N) {
+    // k = (0,0); (0, k2) for k2 = 1..N/2; then k1 = 1..N/2 with all k2 in the disc
+    std::vector<int32_t> h;
+    const int hN = N / 2;
+    auto pack = [](int k1, int k2) { return (int32_t)((uint32_t)(k1 & 0xffff) | ((uint32_t)k2 << 16)); };
+    for (int k2 = 0; k2 <= hN; ++k2) h.push_back(pack(0, k2));
+    for (int k1 = 1; k1 <= hN; ++k1)
+        for (int k2 = -hN; k2 <= hN; ++k2)
+            if (k1 * k1 + k2 * k2 <= hN * hN) h.push_back(pack(k1, k2));
+    return h;
+}
+
+double wavelength_A(double kV) {
+    const double U = kV * 1e3, h = 6.62607015e-34, m = 9.1093837015e-31, e = 1.602176634e-19, c = 299792458.0;
+    return h / std::sqrt(2.0 * m * e * U * (1.0 + e * U / (2.0 * m * c * c))) * 1e10;
+}
+
+double ctf_value(const firm_ctf_group& g, double r) {
+    const double lam = wavelength_A(g.kV);
+    const double cs = g.Cs_mm * 1e7;
+    const double r2 = r * r;
+    const double chi = kPi * lam * g.defocus_A * r2 - 0.5 * kPi * cs * lam * lam * lam * r2 * r2;
+    return -std::sin(chi + g.amp_contrast) * std::exp(-g.bfactor_A2 * r2 / 4.0);
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout
+// ---------------------------------------------------------------------------
+static int disc_size(int N) {
+    int c = 0;
+    const int h = N / 2;
+    for (int k1 = -h; k1 <= h; ++k1)
+        for (int k2 = -h; k2 <= h; ++k2) c += (k1 * k1 + k2 * k2 <= h * h);
+    return c;
+}
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <class T> T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
+    const size_t N = p.N, M = p.M;
+    const size_t nH = (size_t)(disc_size(p.N) + 1) / 2;
+    const size_t n_ctf = p.n_groups > 0 ? (size_t)p.n_groups : 1;
+    const size_t Gk = 4 * N, Gr = 2 * N;
+    const size_t nbk = Gk / kBrick;
+    const size_t nb3 = nbk * nbk * nbk;
+    const size_t max_work = nb3 + M * nH / kChunk + 2;
+    const size_t esz = p.img_dtype == FIRM_IMG_BF16 ? 2 : 4;
+    const size_t N3 = N * N * N, H3 = 2 * N * 2 * N * (N + 1);
+    Carver c{base};
+    w.R = c.take<double>(M * 9);
+    w.shifts = c.take<double>(M * 2);
+    w.gid = c.take<int32_t>(M);
+    w.geom = c.take<ImgGeom>(M);
+    w.htab = c.take<int32_t>(nH);
+    w.h2 = c.take<float>(n_ctf * nH);
+    w.h1 = c.take<float>(n_ctf * nH);
+    w.tw_n = c.take<float2>(N);
+    w.tw_2n = c.take<float2>(2 * N);
+    w.tw_4n = c.take<float2>(4 * N);
+    w.dec_k = c.take<float>(2 * N);
+    w.dec_r = c.take<float>(N);
+    w.samples = c.take<float2>(M * nH);
+    w.count = c.take<uint32_t>(nb3);
+    w.cursor = c.take<uint32_t>(nb3);
+    w.work = c.take<int4>(max_work);
+    w.counters = c.take<int>(8);
+    const size_t grid_bytes = std::max(Gk * Gk * Gk * sizeof(double), Gr * Gr * Gr * 2 * sizeof(double));
+    w.grid = c.take<double>(grid_bytes / sizeof(double));
+    // union: staged images | point ids | FFT intermediates (never live together)
+    const size_t fx1 = std::max({Gk * Gk * (N + 1), Gr * Gr * N, H3});
+    const size_t fx2 = std::max({Gk * 2 * N * (N + 1), Gr * N * N, H3});
+    const size_t u_bytes = std::max({M * N * N * esz, M * nH * sizeof(uint32_t), (fx1 + fx2) * sizeof(float2) + 256});
+    char* u = c.take<char>(u_bytes);
+    w.images = u;
+    w.payload = reinterpret_cast<uint32_t*>(u);
+    w.fx1 = reinterpret_cast<float2*>(u);
+    w.fx2 = u ? reinterpret_cast<float2*>(u + ((fx1 * sizeof(float2) + 255) & ~(size_t)255)) : nullptr;
+    w.ker = c.take<float>(H3);
+    w.khat = c.take<float>(H3);
+    w.rhs = c.take<float>(N3);
+    w.x = c.take<float>(N3);
+    w.r = c.take<float>(N3);
+    w.p = c.take<float>(N3);
+    w.q = c.take<float>(N3);
+    w.t1 = c.take<float2>(N * N * (N + 1));
+    w.t2 = c.take<float2>(N * 2 * N * (N + 1));
+    w.red_a = c.take<double>(kRedSlots);
+    w.red_b = c.take<double>(kRedSlots);
+    w.hist = c.take<double>(kMaxHist);
+    w.cg = c.take<CgState>(1);
+    w.total = c.off + 256;
+    return w.total;
+}
+
+static bool supported_N(int N) {
+    return N == 16 || N == 32 || N == 48 || N == 64 || N == 96 || N == 128;
+}
+
+static int check_params(const firm_params* p) {
+    if (!p) return FIRM_EINVAL;
+    if (!supported_N(p->N)) return FIRM_EINVAL;
+    if (p->M < 0 || p->n_groups < 0) return FIRM_EINVAL;
+    if (p->W < 6 || p->W > 8) return FIRM_EINVAL;
+    if (p->sigma != 2.0) return FIRM_EINVAL;
+    if (p->disc_mode != 0 || p->flags != 0) return FIRM_EINVAL;
+    if (p->img_dtype != FIRM_IMG_F32 && p->img_dtype != FIRM_IMG_BF16) return FIRM_EINVAL;
+    if (p->lambda_mode != FIRM_LAMBDA_RELATIVE && p->lambda_mode != FIRM_LAMBDA_ABSOLUTE) return FIRM_EINVAL;
+    if (!(p->lambda >= 0.0)) return FIRM_EINVAL;
+    const double nH = (disc_size(p->N) + 1) / 2;
+    if ((double)p->M * nH >= 4294967295.0) return FIRM_EINVAL;   // point ids are 32-bit
+    return FIRM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Helpers
+// ---------------------------------------------------------------------------
+static bool is_device(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device pointer for an input: the caller's own if it is device memory, else a copy.
+template <class T>
+static const T* stage(const T* src, T* dst, size_t count, cudaStream_t s, cudaError_t& e) {
+    if (is_device(src)) return src;
+    e = cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s);
+    return dst;
+}
+
+static int put_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (!dst) return FIRM_OK;
+    const bool dev = is_device(dst);
+    if (cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FIRM_ECUDA;
+    if (!dev && cudaStreamSynchronize(s) != cudaSuccess) return FIRM_ECUDA;
+    return FIRM_OK;
+}
+
+struct StageTimer {
+    Plan& P;
+    cudaEvent_t a = nullptr, b = nullptr;
+    explicit StageTimer(Plan& p) : P(p) {
+        if (P.timing) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+        }
+    }
+    void start() { if (P.timing) cudaEventRecord(a, P.stream); }
+    void stop(int slot) {
+        if (!P.timing) return;
+        cudaEventRecord(b, P.stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        P.stage_ms[slot] = ms;
+    }
+    ~StageTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+#define FIRM_CK(x)                                     \
+    do {                                               \
+        if ((x) != cudaSuccess) { return FIRM_ECUDA; } \
+    } while (0)
+
+static int check_spread_flag(Plan& P) {
+    int flag = 0;
+    FIRM_CK(cudaMemcpyAsync(&flag, P.ws.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    return flag ? FIRM_ECUDA : FIRM_OK;
+}
+
+}  // namespace firm
+
+using namespace firm;
+
+struct firm_plan_s {
+    Plan P;
+};
+
+extern "C" {
+
+int firm_workspace_size(const firm_params* p, size_t* bytes) {
+    const int st = check_params(p);
+    if (st != FIRM_OK) return st;
+    if (!bytes) return FIRM_EINVAL;
+    Workspace w;
+    *bytes = layout_workspace(*p, nullptr, w);
+    return FIRM_OK;
+}
+
+int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* groups, void* workspace,
+              size_t workspace_bytes, void* stream) {
+    if (!out) return FIRM_EINVAL;
+    *out = nullptr;
+    int st = check_params(p);
+    if (st != FIRM_OK) return st;
+    if (p->n_groups > 0 && !groups) return FIRM_EINVAL;
+    Workspace probe;
+    const size_t need = layout_workspace(*p, nullptr, probe);
+    if (!workspace || workspace_bytes < need) return FIRM_ENOMEM;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return FIRM_EINVAL;
+    if (!is_device(workspace)) return FIRM_EINVAL;
+
+    firm_plan_s* h = new (std::nothrow) firm_plan_s();
+    if (!h) return FIRM_ENOMEM;
+    Plan& P = h->P;
+    P.p = *p;
+    P.stream = reinterpret_cast<cudaStream_t>(stream);
+    P.base = reinterpret_cast<char*>(workspace);
+    layout_workspace(*p, P.base, P.ws);
+    P.N = p->N;
+    P.Gk = 4 * p->N;
+    P.Gr = 2 * p->N;
+    P.nbk = P.Gk / kBrick;
+    P.nbr = P.Gr / kBrick;
+    P.nK = disc_size(p->N);
+    P.nH = (P.nK + 1) / 2;
+    P.n_ctf = p->n_groups > 0 ? p->n_groups : 1;
+    P.max_work = (size_t)P.nbk * P.nbk * P.nbk + (size_t)p->M * P.nH / kChunk + 2;
+    for (int g = 0; g < p->n_groups; ++g) P.groups.push_back(groups[g]);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete h;
+        return FIRM_ECUDA;
+    }
+    if (fft_init_constants() != cudaSuccess) { delete h; return FIRM_ECUDA; }
+
+    double beta = 0.0;
+    kb_build(p->W, p->sigma, P.poly, &beta);
+
+    // tables
+    const int N = P.N, nH = P.nH;
+    P.htab_host = half_disc(N);
+    std::vector<float> h1((size_t)P.n_ctf * nH), h2((size_t)P.n_ctf * nH);
+    for (int g = 0; g < P.n_ctf; ++g) {
+        for (int t = 0; t < nH; ++t) {
+            const int32_t kk = P.htab_host[t];
+            const int k1 = (int16_t)(kk & 0xffff), k2 = kk >> 16;
+            double hv = 1.0;
+            if (p->n_groups > 0) hv = ctf_value(P.groups[g], std::sqrt((double)(k1 * k1 + k2 * k2)) / (N * P.groups[g].pixel_A));
+            h1[(size_t)g * nH + t] = (float)hv;
+            h2[(size_t)g * nH + t] = (float)(hv * hv * (t == 0 ? 0.5 : 1.0));
+        }
+    }
+    auto tw = [](int L) {
+        std::vector<float2> v(L);
+        for (int j = 0; j < L; ++j) {
+            const double a = -2.0 * kPi * j / L;
+            v[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        return v;
+    };
+    // deconvolution: (-1)^n / phihat(n / G) for the centred fine grid
+    std::vector<float> dk(2 * N), dr(N);
+    for (int i = 0; i < 2 * N; ++i) {
+        const int n = i - N;
+        dk[i] = (float)(((n & 1) ? -1.0 : 1.0) / kb_phihat((double)n / P.Gk, p->W, beta));
+    }
+    for (int i = 0; i < N; ++i) {
+        const int n = i - N / 2;
+        dr[i] = (float)(((n & 1) ? -1.0 : 1.0) / kb_phihat((double)n / P.Gr, p->W, beta));
+    }
+    const std::vector<float2> t1 = tw(N), t2 = tw(2 * N), t4 = tw(4 * N);
+    Workspace& w = P.ws;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* d, const void* s, size_t b) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d, s, b, cudaMemcpyHostToDevice, P.stream);
+    };
+    cp(w.htab, P.htab_host.data(), sizeof(int32_t) * nH);
+    cp(w.h1, h1.data(), sizeof(float) * h1.size());
+    cp(w.h2, h2.data(), sizeof(float) * h2.size());
+    cp(w.tw_n, t1.data(), sizeof(float2) * N);
+    cp(w.tw_2n, t2.data(), sizeof(float2) * 2 * N);
+    cp(w.tw_4n, t4.data(), sizeof(float2) * 4 * N);
+    cp(w.dec_k, dk.data(), sizeof(float) * dk.size());
+    cp(w.dec_r, dr.data(), sizeof(float) * dr.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), P.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
+    if (e != cudaSuccess) {
+        delete h;
+        return FIRM_ECUDA;
+    }
+    *out = h;
+    return FIRM_OK;
+}
+
+int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, float* khat_out) {
+    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && !R)) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    Workspace& w = P.ws;
+    cudaError_t e = cudaSuccess;
+    StageTimer tm(P);
+    P.cur_R = stage(R, w.R, (size_t)M * 9, P.stream, e);
+    if (group) P.cur_gid = stage(group, w.gid, (size_t)M, P.stream, e);
+    else { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
+    FIRM_CK(e);
+    FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
+    tm.start();
+    FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
+    FIRM_CK(launch_bin(P, M, true));
+    tm.stop(0);
+    tm.start();
+    FIRM_CK(launch_spread(P, M, true));
+    tm.stop(1);
+    tm.start();
+    FIRM_CK(launch_ker_transform(P));
+    tm.stop(2);
+    tm.start();
+    FIRM_CK(launch_khat(P));
+    tm.stop(3);
+    // lam_eff from Ker(0) (the n = 0 entry of the half box)
+    float ker0 = 0.f;
+    const size_t i0 = ((size_t)P.N * 2 * P.N + P.N) * (P.N + 1);
+    FIRM_CK(cudaMemcpyAsync(&ker0, w.ker + i0, sizeof(float), cudaMemcpyDeviceToHost, P.stream));
+    int st = check_spread_flag(P);
+    if (st != FIRM_OK) return st;
+    P.lam_eff = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda * (double)ker0 : P.p.lambda;
+    P.have_kernel = true;
+    return put_out(khat_out, w.khat, sizeof(float) * 2 * P.N * 2 * P.N * (P.N + 1), P.stream);
+}
+
+int firm_backproject(firm_plan_t plan, int M, const void* images, const double* shifts, const double* R,
+                     const int32_t* group, float* rhs_out) {
+    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !images))) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    Workspace& w = P.ws;
+    cudaError_t e = cudaSuccess;
+    StageTimer tm(P);
+    const size_t esz = P.p.img_dtype == FIRM_IMG_BF16 ? 2 : 4;
+    P.cur_R = stage(R, w.R, (size_t)M * 9, P.stream, e);
+    if (group) P.cur_gid = stage(group, w.gid, (size_t)M, P.stream, e);
+    else { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
+    if (shifts) P.cur_shifts = stage(shifts, w.shifts, (size_t)M * 2, P.stream, e);
+    else { if (e == cudaSuccess) e = cudaMemsetAsync(w.shifts, 0, sizeof(double) * 2 * (M > 0 ? M : 1), P.stream); P.cur_shifts = w.shifts; }
+    FIRM_CK(e);
+    if (M > 0 && !is_device(images)) {
+        FIRM_CK(cudaMemcpyAsync(w.images, images, (size_t)M * P.N * P.N * esz, cudaMemcpyHostToDevice, P.stream));
+        P.cur_images = w.images;
+    } else {
+        P.cur_images = images;
+    }
+    FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
+    tm.start();
+    FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
+    FIRM_CK(launch_image_dft(P, M, P.cur_images, P.cur_shifts, P.cur_gid));
+    tm.stop(4);
+    tm.start();
+    FIRM_CK(launch_bin(P, M, false));
+    tm.stop(0);
+    tm.start();
+    FIRM_CK(launch_spread(P, M, false));
+    tm.stop(1);
+    tm.start();
+    FIRM_CK(launch_rhs_transform(P));
+    tm.stop(2);
+    int st = check_spread_flag(P);
+    if (st != FIRM_OK) return st;
+    P.have_rhs = true;
+    return put_out(rhs_out, w.rhs, sizeof(float) * P.N * P.N * P.N, P.stream);
+}
+
+int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y) {
+    if (!plan || !x || !y) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!P.have_kernel) return FIRM_ESTATE;
+    Workspace& w = P.ws;
+    const size_t n = (size_t)P.N * P.N * P.N;
+    cudaError_t e = cudaSuccess;
+    const float* xd = stage(x, w.x, n, P.stream, e);
+    FIRM_CK(e);
+    const bool ydev = is_device(y);
+    float* yd = ydev ? y : w.q;
+    if (xd == yd) return FIRM_EINVAL;
+    FIRM_CK(launch_toeplitz(P, xd, yd, (float)P.lam_eff, nullptr, nullptr));
+    if (!ydev) return put_out(y, yd, n * sizeof(float), P.stream);
+    return FIRM_OK;
+}
+
+int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, double rel_tol, double* resid_hist,
+                  int* iters_out) {
+    if (!plan || !x || max_iter < 0 || max_iter >= kMaxHist || !(rel_tol >= 0.0)) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!P.have_kernel) return FIRM_ESTATE;
+    if (!rhs && !P.have_rhs) return FIRM_ESTATE;
+    Workspace& w = P.ws;
+    const size_t n = (size_t)P.N * P.N * P.N;
+    cudaError_t e = cudaSuccess;
+    const float* rd = rhs ? stage(rhs, w.q, n, P.stream, e) : w.rhs;
+    FIRM_CK(e);
+    StageTimer tm(P);
+    tm.start();
+    FIRM_CK(launch_cg_init(P, rd, max_iter, rel_tol));
+    const int batch = 8;
+    for (int it = 0; it < max_iter; ++it) {
+        FIRM_CK(launch_toeplitz(P, w.p, w.q, (float)P.lam_eff, w.r, w.cg));
+        FIRM_CK(launch_cg_update(P));
+        if (rel_tol > 0.0 && ((it + 1) % batch == 0) && it + 1 < max_iter) {
+            int done = 0;
+            FIRM_CK(cudaMemcpyAsync(&done, &w.cg->done, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+            FIRM_CK(cudaStreamSynchronize(P.stream));
+            if (done) break;
+        }
+    }
+    tm.stop(5);
+    CgState s;
+    FIRM_CK(cudaMemcpyAsync(&s, w.cg, sizeof(CgState), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    P.stage_ms[6] = s.it;
+    if (resid_hist) {
+        const bool dev = is_device(resid_hist);
+        FIRM_CK(cudaMemcpyAsync(resid_hist, w.hist, sizeof(double) * (s.it + 1),
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P.stream));
+    }
+    if (iters_out) *iters_out = s.it;
+    int st = put_out(x, w.x, n * sizeof(float), P.stream);
+    if (st != FIRM_OK) return st;
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    if (s.status != FIRM_OK) return s.status;
+    if (rel_tol > 0.0 && !(s.rr >= 0.0 && std::sqrt(s.rr) <= s.tol)) return FIRM_ENOTCONV;
+    return FIRM_OK;
+}
+
+int firm_lambda_eff(firm_plan_t plan, double* out) {
+    if (!plan || !out) return FIRM_EINVAL;
+    if (!plan->P.have_kernel) return FIRM_ESTATE;
+    *out = plan->P.lam_eff;
+    return FIRM_OK;
+}
+
+int firm_copy_out(firm_plan_t plan, int which, void* dst) {
+    if (!plan || !dst) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    const size_t N = P.N, H3 = 2 * N * 2 * N * (N + 1);
+    switch (which) {
+        case FIRM_OUT_KER: return P.have_kernel ? put_out(dst, P.ws.ker, H3 * sizeof(float), P.stream) : FIRM_ESTATE;
+        case FIRM_OUT_KHAT: return P.have_kernel ? put_out(dst, P.ws.khat, H3 * sizeof(float), P.stream) : FIRM_ESTATE;
+        case FIRM_OUT_RHS: return P.have_rhs ? put_out(dst, P.ws.rhs, N * N * N * sizeof(float), P.stream) : FIRM_ESTATE;
+        case FIRM_OUT_SAMPLES:
+            return P.have_rhs ? put_out(dst, P.ws.samples, (size_t)P.p.M * P.nH * sizeof(float2), P.stream) : FIRM_ESTATE;
+        default: return FIRM_EINVAL;
+    }
+}
+
+int firm_set_timing(firm_plan_t plan, int on) {
+    if (!plan) return FIRM_EINVAL;
+    plan->P.timing = on != 0;
+    return FIRM_OK;
+}
+
+int firm_stage_times(firm_plan_t plan, double* out7) {
+    if (!plan || !out7) return FIRM_EINVAL;
+    for (int i = 0; i < 7; ++i) out7[i] = plan->P.stage_ms[i];
+    return FIRM_OK;
+}
+
+void firm_destroy(firm_plan_t plan) { delete plan; }
+
+const char* firm_strerror(int code) {
+    switch (code) {
+        case FIRM_OK: return "ok";
+        case FIRM_EINVAL: return "invalid argument";
+        case FIRM_ENOMEM: return "workspace too small";
+        case FIRM_ECUDA: return "CUDA error";
+        case FIRM_ENOTCONV: return "CG did not reach the relative tolerance";
+        case FIRM_EBREAKDOWN: return "CG breakdown";
+        case FIRM_ETIMEOUT: return "device wait timed out";
+        case FIRM_ESTATE: return "call order (kernel or right-hand side missing)";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

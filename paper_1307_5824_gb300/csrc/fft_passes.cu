@@ -1,0 +1,536 @@
+// fft_passes.cu -- every FFT-based stage of the FIRM hot path.
+//
+//   image DFT   FIRM step 1 (Section 3.4; Section 2.2 centred DFT, eq. measurement):
+//               one CTA per image, row then column transforms in shared memory, the
+//               half-disc samples times h_m and the shift phase written out.
+//   Ker         eq. kernel: the 4N^3 fine grid (FP64) transformed along x, y, z with
+//               output pruning to n in [-N, N) (n1 >= 0 by Ker(-n) = Ker(n)),
+//               Ker = 2 Re(ghat) / phihat (the factor 2 adds the mirrored half disc).
+//   K-hat       eq. embedding_circulant / eq. circ1: the 2N^3 circulant column gathered
+//               from the Ker half box, transformed, real part kept on j1 in [0, N].
+//   A*b         eq. backprojection: 2N^3 complex fine grid -> N^3, 2 Re / phihat.
+//   Toeplitz    eq. property via Section 3.2: x padded to 2N^3, forward along x (real
+//               rows, half spectrum kept), y, then z-forward x K-hat x z-inverse in one
+//               pass, y-inverse and x-inverse (Hermitian rows) with the crop, 1/(2N)^3
+//               and lam_eff x fused; optionally the CG update p = r + beta p in the
+//               first pass and the FP64 partial sums of <p, Ap> in the last.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "firm_internal.h"
+
+namespace firm {
+
+
+cudaError_t fft_init_constants() {
+    float2 h[kTwConstTotal];
+    const int sizes[] = {4, 6, 8, 10, 12, 16, 20, 24, 32};
+    for (int R : sizes) {
+        const int off = tw_offset(R);
+        for (int j = 0; j < R; ++j) {
+            const double a = -2.0 * 3.14159265358979323846 * (double)j / (double)R;
+            h[off + j] = make_float2((float)cos(a), (float)sin(a));
+        }
+    }
+    return cudaMemcpyToSymbol(c_tw, h, sizeof(h));
+}
+
+constexpr int kTX = 16;          // lines per tile of a column pass
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Generic pass kernels.  An Op provides n_outer, n_inner / n_rows, tw, load, store.
+// ---------------------------------------------------------------------------
+template <int L, int SIGN, class Op>
+__global__ void __launch_bounds__(kThreads) k_cols(const Op op) {
+    extern __shared__ float2 S[];
+    const int tiles = (op.n_inner + kTX - 1) / kTX;
+    const int outer = blockIdx.x / tiles;
+    const int c0 = (blockIdx.x % tiles) * kTX;
+    const int nl = min(kTX, op.n_inner - c0);
+    auto ld = [&](int line, int n) { return op.load(outer, n, c0 + line); };
+    auto st = [&](int line, int k, float2 v) { op.store(outer, k, c0 + line, v); };
+    block_fft<L, SIGN, true>(nl, ld, st, S, op.tw);
+}
+
+template <int L> __host__ __device__ constexpr int rows_per_block() { return kThreads / Split<L>::L2; }
+
+template <int L, int SIGN, class Op>
+__global__ void __launch_bounds__(kThreads) k_rows(Op op) {
+    extern __shared__ float2 S[];
+    constexpr int ROWS = rows_per_block<L>();
+    const int r0 = blockIdx.x * ROWS;
+    const int nl = min(ROWS, op.n_rows - r0);
+    auto ld = [&](int line, int n) { return op.load(r0 + line, n); };
+    auto st = [&](int line, int k, float2 v) { op.store(r0 + line, k, v); };
+    block_fft<L, SIGN, false>(nl, ld, st, S, op.tw);
+    op.finish();
+}
+
+template <int L, int SIGN, class Op>
+static cudaError_t run_cols(const Op& op, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * smem_elems<L, true>(kTX);
+    cudaError_t e = cudaFuncSetAttribute(k_cols<L, SIGN, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = (op.n_inner + kTX - 1) / kTX;
+    k_cols<L, SIGN, Op><<<op.n_outer * tiles, kThreads, smem, s>>>(op);
+    return cudaGetLastError();
+}
+
+template <int L, int SIGN, class Op>
+static cudaError_t run_rows(const Op& op, cudaStream_t s) {
+    constexpr int ROWS = rows_per_block<L>();
+    const size_t smem = sizeof(float2) * smem_elems<L, false>(ROWS);
+    cudaError_t e = cudaFuncSetAttribute(k_rows<L, SIGN, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_rows<L, SIGN, Op><<<(op.n_rows + ROWS - 1) / ROWS, kThreads, smem, s>>>(op);
+    return cudaGetLastError();
+}
+
+struct NoFinish {
+    __device__ __forceinline__ void finish() const {}
+};
+
+// Transform lengths instantiated: 2N and 4N for N in {16, 32, 48, 64, 96, 128}.
+#define FIRM_CASE_L(V, ...) case V: { constexpr int LL = V; __VA_ARGS__; } break;
+#define FIRM_SWITCH_2N(Lval, ...)                                                             \
+    switch (Lval) {                                                                          \
+        FIRM_CASE_L(32, __VA_ARGS__) FIRM_CASE_L(64, __VA_ARGS__) FIRM_CASE_L(96, __VA_ARGS__)   \
+        FIRM_CASE_L(128, __VA_ARGS__) FIRM_CASE_L(192, __VA_ARGS__) FIRM_CASE_L(256, __VA_ARGS__) \
+        default: return cudaErrorInvalidValue;                                               \
+    }
+#define FIRM_SWITCH_4N(Lval, ...)                                                             \
+    switch (Lval) {                                                                          \
+        FIRM_CASE_L(64, __VA_ARGS__) FIRM_CASE_L(128, __VA_ARGS__) FIRM_CASE_L(192, __VA_ARGS__) \
+        FIRM_CASE_L(256, __VA_ARGS__) FIRM_CASE_L(384, __VA_ARGS__) FIRM_CASE_L(512, __VA_ARGS__) \
+        default: return cudaErrorInvalidValue;                                               \
+    }
+
+// ---------------------------------------------------------------------------
+// Ker: 4N^3 real FP64 grid -> Ker half box
+// ---------------------------------------------------------------------------
+struct KerRowsOp : NoFinish {
+    const double* grid; float2* out; const float2* tw; int n_rows, G, N;
+    __device__ __forceinline__ float2 load(int row, int n) const {
+        return make_float2((float)__ldg(&grid[(size_t)row * G + n]), 0.0f);
+    }
+    __device__ __forceinline__ void store(int row, int k, float2 v) const {
+        if (k <= N) out[(size_t)row * (N + 1) + k] = v;
+    }
+};
+struct KerColsYOp {
+    const float2* in; float2* out; const float2* tw; int n_outer, n_inner, G, N;
+    __device__ __forceinline__ float2 load(int o, int n, int i) const {
+        return __ldg(&in[((size_t)o * G + n) * (N + 1) + i]);
+    }
+    __device__ __forceinline__ void store(int o, int k, int i, float2 v) const {
+        const int n2 = k < N ? k : (k >= G - N ? k - G : G);
+        if (n2 != G) out[((size_t)o * 2 * N + (n2 + N)) * (N + 1) + i] = v;
+    }
+};
+struct KerColsZOp {
+    const float2* in; float* ker; const float* dec; const float2* tw; int n_outer, n_inner, G, N;
+    __device__ __forceinline__ float2 load(int, int n, int i) const { return __ldg(&in[(size_t)n * n_inner + i]); }
+    __device__ __forceinline__ void store(int, int k, int i, float2 v) const {
+        const int n3 = k < N ? k : (k >= G - N ? k - G : G);
+        if (n3 == G) return;
+        const int n2i = i / (N + 1), n1 = i - n2i * (N + 1);
+        ker[(size_t)(n3 + N) * n_inner + i] = 2.0f * v.x * __ldg(&dec[n1 + N]) * __ldg(&dec[n2i]) * __ldg(&dec[n3 + N]);
+    }
+};
+
+cudaError_t launch_ker_transform(Plan& P) {
+    Workspace& w = P.ws;
+    const int N = P.N, G = P.Gk;
+    cudaError_t e = cudaSuccess;
+    KerRowsOp a{{}, w.grid, w.fx1, w.tw_4n, G * G, G, N};
+    KerColsYOp b{w.fx1, w.fx2, w.tw_4n, G, N + 1, G, N};
+    KerColsZOp c{w.fx2, w.ker, w.dec_k, w.tw_4n, 1, 2 * N * (N + 1), G, N};
+    FIRM_SWITCH_4N(G, {
+        if ((e = run_rows<LL, +1>(a, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, +1>(b, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, +1>(c, P.stream)) != cudaSuccess) return e;
+    });
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// K-hat: circulant column (reading: lag-N planes zero) -> 2N^3 forward FFT, real part
+// ---------------------------------------------------------------------------
+struct KhatRowsOp : NoFinish {
+    const float* ker; float2* out; const float2* tw; int n_rows, N;
+    __device__ __forceinline__ float2 load(int row, int i1) const {
+        const int N2 = 2 * N;
+        const int i3 = row / N2, i2 = row - i3 * N2;
+        if (i1 == N || i2 == N || i3 == N) return make_float2(0.0f, 0.0f);
+        const int d1 = i1 < N ? i1 : i1 - N2;
+        const int d2 = i2 < N ? i2 : i2 - N2;
+        const int d3 = i3 < N ? i3 : i3 - N2;
+        size_t idx;
+        if (d1 >= 0) idx = ((size_t)(d3 + N) * N2 + (d2 + N)) * (N + 1) + d1;
+        else idx = ((size_t)(N - d3) * N2 + (N - d2)) * (N + 1) + (-d1);
+        return make_float2(__ldg(&ker[idx]), 0.0f);
+    }
+    __device__ __forceinline__ void store(int row, int k, float2 v) const {
+        if (k <= N) out[(size_t)row * (N + 1) + k] = v;
+    }
+};
+struct KhatColsYOp {
+    const float2* in; float2* out; const float2* tw; int n_outer, n_inner, L;
+    __device__ __forceinline__ float2 load(int o, int n, int i) const {
+        return __ldg(&in[((size_t)o * L + n) * n_inner + i]);
+    }
+    __device__ __forceinline__ void store(int o, int k, int i, float2 v) const {
+        out[((size_t)o * L + k) * n_inner + i] = v;
+    }
+};
+struct KhatColsZOp {
+    const float2* in; float* khat; const float2* tw; int n_outer, n_inner;
+    __device__ __forceinline__ float2 load(int, int n, int i) const { return __ldg(&in[(size_t)n * n_inner + i]); }
+    __device__ __forceinline__ void store(int, int k, int i, float2 v) const { khat[(size_t)k * n_inner + i] = v.x; }
+};
+
+cudaError_t launch_khat(Plan& P) {
+    Workspace& w = P.ws;
+    const int N = P.N, L = 2 * N;
+    cudaError_t e = cudaSuccess;
+    KhatRowsOp a{{}, w.ker, w.fx1, w.tw_2n, L * L, N};
+    KhatColsYOp b{w.fx1, w.fx2, w.tw_2n, L, N + 1, L};
+    KhatColsZOp c{w.fx2, w.khat, w.tw_2n, 1, L * (N + 1)};
+    FIRM_SWITCH_2N(L, {
+        if ((e = run_rows<LL, -1>(a, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, -1>(b, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, -1>(c, P.stream)) != cudaSuccess) return e;
+    });
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// A*b: 2N^3 complex FP64 grid -> N^3 real
+// ---------------------------------------------------------------------------
+struct RhsRowsOp : NoFinish {
+    const double* grid; float2* out; const float2* tw; int n_rows, G, N;
+    __device__ __forceinline__ float2 load(int row, int n) const {
+        const double2 g = __ldg(reinterpret_cast<const double2*>(grid) + (size_t)row * G + n);
+        return make_float2((float)g.x, (float)g.y);
+    }
+    __device__ __forceinline__ void store(int row, int k, float2 v) const {
+        const int h = N / 2;
+        const int n1 = k < h ? k : (k >= G - h ? k - G : G);
+        if (n1 != G) out[(size_t)row * N + (n1 + h)] = v;
+    }
+};
+struct RhsColsYOp {
+    const float2* in; float2* out; const float2* tw; int n_outer, n_inner, G, N;
+    __device__ __forceinline__ float2 load(int o, int n, int i) const {
+        return __ldg(&in[((size_t)o * G + n) * N + i]);
+    }
+    __device__ __forceinline__ void store(int o, int k, int i, float2 v) const {
+        const int h = N / 2;
+        const int n2 = k < h ? k : (k >= G - h ? k - G : G);
+        if (n2 != G) out[((size_t)o * N + (n2 + h)) * N + i] = v;
+    }
+};
+struct RhsColsZOp {
+    const float2* in; float* rhs; const float* dec; const float2* tw; int n_outer, n_inner, G, N;
+    __device__ __forceinline__ float2 load(int, int n, int i) const { return __ldg(&in[(size_t)n * n_inner + i]); }
+    __device__ __forceinline__ void store(int, int k, int i, float2 v) const {
+        const int h = N / 2;
+        const int n3 = k < h ? k : (k >= G - h ? k - G : G);
+        if (n3 == G) return;
+        const int n2i = i / N, n1i = i - n2i * N;
+        rhs[(size_t)(n3 + h) * n_inner + i] = 2.0f * v.x * __ldg(&dec[n1i]) * __ldg(&dec[n2i]) * __ldg(&dec[n3 + h]);
+    }
+};
+
+cudaError_t launch_rhs_transform(Plan& P) {
+    Workspace& w = P.ws;
+    const int N = P.N, G = P.Gr;
+    cudaError_t e = cudaSuccess;
+    RhsRowsOp a{{}, w.grid, w.fx1, w.tw_2n, G * G, G, N};
+    RhsColsYOp b{w.fx1, w.fx2, w.tw_2n, G, N, G, N};
+    RhsColsZOp c{w.fx2, w.rhs, w.dec_r, w.tw_2n, 1, N * N, G, N};
+    FIRM_SWITCH_2N(G, {
+        if ((e = run_rows<LL, +1>(a, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, +1>(b, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, +1>(c, P.stream)) != cudaSuccess) return e;
+    });
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Image DFT (FIRM step 1)
+// ---------------------------------------------------------------------------
+struct ImgArgs {
+    const void* images; const double* shifts; const int32_t* gid; const int32_t* htab;
+    const float* h1; float2* samples; const float2* tw; int nH, n_ctf;
+};
+
+template <int N, class T>
+__device__ __forceinline__ float img_val(const void* p, size_t i) {
+    if constexpr (sizeof(T) == 2) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[i]);
+    else return __ldg(reinterpret_cast<const float*>(p) + i);
+}
+
+template <int N> __host__ __device__ constexpr int img_rows() { return kThreads / Split<N>::L2; }
+template <int N> __host__ __device__ constexpr int img_smem_elems() {
+    constexpr int a = smem_elems<N, false>(img_rows<N>());
+    constexpr int b = smem_elems<N, true>(kTX);
+    return N * (N / 2 + 1) + (a > b ? a : b);
+}
+
+template <int N, class T>
+__global__ void __launch_bounds__(kThreads) k_image_dft(const ImgArgs a) {
+    extern __shared__ float2 sm2[];
+    constexpr int H1 = N / 2 + 1;
+    float2* S1 = sm2;
+    float2* scr = sm2 + N * H1;
+    const int m = blockIdx.x;
+    const size_t img0 = (size_t)m * N * N;
+    constexpr int ROWS = img_rows<N>();
+    for (int r0 = 0; r0 < N; r0 += ROWS) {
+        const int nl = min(ROWS, N - r0);
+        auto ld = [&](int line, int n) { return make_float2(img_val<N, T>(a.images, img0 + (size_t)(r0 + line) * N + n), 0.0f); };
+        auto st = [&](int line, int k, float2 v) { if (k <= N / 2) S1[(r0 + line) * H1 + k] = v; };
+        block_fft<N, -1, false>(nl, ld, st, scr, a.tw);
+    }
+    for (int c0 = 0; c0 < H1; c0 += kTX) {
+        const int nl = min(kTX, H1 - c0);
+        auto ld = [&](int line, int n) { return S1[n * H1 + c0 + line]; };
+        auto st = [&](int line, int k, float2 v) { S1[k * H1 + c0 + line] = v; };
+        block_fft<N, -1, true>(nl, ld, st, scr, a.tw);
+    }
+    // half-disc samples: centred index sign, CTF, shift phase, k = 0 halved
+    const int g = a.gid ? min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1) : 0;
+    const float s1 = (float)(2.0 * a.shifts[2 * m] / N), s2 = (float)(2.0 * a.shifts[2 * m + 1] / N);
+    for (int t = threadIdx.x; t < a.nH; t += blockDim.x) {
+        const int kk = __ldg(&a.htab[t]);
+        const int k1 = (int16_t)(kk & 0xffff), k2 = kk >> 16;
+        float2 v = S1[((k2 + N) % N) * H1 + k1];
+        float hs = __ldg(&a.h1[(size_t)g * a.nH + t]);
+        if ((k1 + k2) & 1) hs = -hs;
+        if (t == 0) hs *= 0.5f;
+        float sn, cs;
+        sincospif((float)k1 * s1 + (float)k2 * s2, &sn, &cs);
+        const float2 ph = make_float2(cs * hs, sn * hs);
+        a.samples[(size_t)m * a.nH + t] = c_mul(v, ph);
+    }
+}
+
+template <int N, class T>
+static cudaError_t image_dft_n(Plan& P, int M, const ImgArgs& a) {
+    const size_t smem = sizeof(float2) * img_smem_elems<N>();
+    cudaError_t e = cudaFuncSetAttribute(k_image_dft<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_image_dft<N, T><<<M, kThreads, smem, P.stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* shifts, const int32_t* gid) {
+    if (M <= 0) return cudaSuccess;
+    ImgArgs a{images, shifts, gid, P.ws.htab, P.ws.h1, P.ws.samples, P.ws.tw_n, P.nH, P.n_ctf};
+    const bool bf = P.p.img_dtype == FIRM_IMG_BF16;
+    switch (P.N) {
+        case 16: return bf ? image_dft_n<16, uint16_t>(P, M, a) : image_dft_n<16, float>(P, M, a);
+        case 32: return bf ? image_dft_n<32, uint16_t>(P, M, a) : image_dft_n<32, float>(P, M, a);
+        case 48: return bf ? image_dft_n<48, uint16_t>(P, M, a) : image_dft_n<48, float>(P, M, a);
+        case 64: return bf ? image_dft_n<64, uint16_t>(P, M, a) : image_dft_n<64, float>(P, M, a);
+        case 96: return bf ? image_dft_n<96, uint16_t>(P, M, a) : image_dft_n<96, float>(P, M, a);
+        case 128: return bf ? image_dft_n<128, uint16_t>(P, M, a) : image_dft_n<128, float>(P, M, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Toeplitz apply (CG-fused when cg != nullptr)
+// ---------------------------------------------------------------------------
+struct TRowsFwdOp : NoFinish {
+    const float* x; float* p; const float* r; const CgState* cg; float2* out; const float2* tw; int n_rows, N;
+    __device__ __forceinline__ float2 load(int row, int n) const {
+        if (n >= N) return make_float2(0.0f, 0.0f);
+        const size_t i = (size_t)row * N + n;
+        if (cg) {   // p = r + beta p, written back
+            const float v = __ldg(&r[i]) + (float)cg->beta * p[i];
+            p[i] = v;
+            return make_float2(v, 0.0f);
+        }
+        return make_float2(__ldg(&x[i]), 0.0f);
+    }
+    __device__ __forceinline__ void store(int row, int k, float2 v) const {
+        if (k <= N) out[(size_t)row * (N + 1) + k] = v;
+    }
+};
+struct TColsYFwdOp {
+    const float2* in; float2* out; const float2* tw; int n_outer, n_inner, N;
+    __device__ __forceinline__ float2 load(int o, int n, int i) const {
+        return n < N ? __ldg(&in[((size_t)o * N + n) * (N + 1) + i]) : make_float2(0.0f, 0.0f);
+    }
+    __device__ __forceinline__ void store(int o, int k, int i, float2 v) const {
+        out[((size_t)o * 2 * N + k) * (N + 1) + i] = v;
+    }
+};
+struct TColsYInvOp {
+    const float2* in; float2* out; const float2* tw; int n_outer, n_inner, N;
+    __device__ __forceinline__ float2 load(int o, int n, int i) const {
+        return __ldg(&in[((size_t)o * 2 * N + n) * (N + 1) + i]);
+    }
+    __device__ __forceinline__ void store(int o, int k, int i, float2 v) const {
+        if (k < N) out[((size_t)o * N + k) * (N + 1) + i] = v;
+    }
+};
+struct TRowsInvOp {
+    const float2* in; const float* x; float* y; double* red; CgState* cg; const float2* tw;
+    int n_rows, N; float scale, lam;
+    double* acc;   // per-thread partial <x, y> (CG)
+    __device__ __forceinline__ float2 load(int row, int n) const {
+        const float2* rr = in + (size_t)row * (N + 1);
+        return n <= N ? __ldg(&rr[n]) : c_conj(__ldg(&rr[2 * N - n]));
+    }
+    __device__ __forceinline__ void store(int row, int k, float2 v) const {
+        if (k >= N) return;
+        const size_t i = (size_t)row * N + k;
+        const float xv = __ldg(&x[i]);
+        const float yv = fmaf(v.x, scale, lam * xv);
+        y[i] = yv;
+        if (cg) *acc += (double)xv * (double)yv;
+    }
+    __device__ __forceinline__ void finish() const {}
+};
+
+// The z pass: forward, times K-hat, inverse; tile of kTX adjacent (j2, j1) columns.
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_toep_z(float2* __restrict__ t2, const float* __restrict__ khat,
+                                                     const float2* __restrict__ tw, int n_inner, int N,
+                                                     const CgState* cg) {
+    extern __shared__ float2 S[];
+    if (cg && cg->done) return;
+    const int c0 = blockIdx.x * kTX;
+    const int nl = min(kTX, n_inner - c0);
+    auto ld = [&](int line, int n) {
+        return n < N ? t2[(size_t)n * n_inner + c0 + line] : make_float2(0.0f, 0.0f);
+    };
+    auto mul = [&](int line, int k) { return __ldg(&khat[(size_t)k * n_inner + c0 + line]); };
+    auto st = [&](int line, int n, float2 v) {
+        if (n < N) t2[(size_t)n * n_inner + c0 + line] = v;
+    };
+    block_fft_mul_ifft<L>(nl, ld, mul, st, S, tw);
+}
+
+// Last pass of the apply with the CG reduction of <p, Ap> (last-block pattern).
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_toep_rows_inv(TRowsInvOp op) {
+    extern __shared__ float2 S[];
+    __shared__ double s_red[kThreads / 32];
+    __shared__ bool s_last;
+    if (op.cg && op.cg->done) return;
+    constexpr int ROWS = rows_per_block<L>();
+    const int r0 = blockIdx.x * ROWS;
+    const int nl = min(ROWS, op.n_rows - r0);
+    double acc = 0.0;
+    op.acc = &acc;
+    auto ld = [&](int line, int n) { return op.load(r0 + line, n); };
+    auto st = [&](int line, int k, float2 v) { op.store(r0 + line, k, v); };
+    block_fft<L, +1, false>(nl, ld, st, S, op.tw);
+    if (!op.cg) return;
+    // block reduction
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) b += s_red[i];
+        op.red[blockIdx.x] = b;
+        __threadfence();
+        const unsigned t = atomicAdd(&op.cg->ticket_a, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // deterministic final sum over block partials, in block order
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)op.red)[i];
+    // fixed-order tree over threads
+    __shared__ double s_fin[kThreads];
+    s_fin[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) s_fin[threadIdx.x] += s_fin[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        op.cg->pq = s_fin[0];
+        op.cg->ticket_a = 0;
+    }
+}
+
+template <int L, class Op>
+__global__ void __launch_bounds__(kThreads) k_rows_cg(Op op, const CgState* cg) {
+    extern __shared__ float2 S[];
+    if (cg && cg->done) return;
+    constexpr int ROWS = rows_per_block<L>();
+    const int r0 = blockIdx.x * ROWS;
+    const int nl = min(ROWS, op.n_rows - r0);
+    auto ld = [&](int line, int n) { return op.load(r0 + line, n); };
+    auto st = [&](int line, int k, float2 v) { op.store(r0 + line, k, v); };
+    block_fft<L, -1, false>(nl, ld, st, S, op.tw);
+}
+
+template <int L, int SIGN, class Op>
+__global__ void __launch_bounds__(kThreads) k_cols_cg(const Op op, const CgState* cg) {
+    extern __shared__ float2 S[];
+    if (cg && cg->done) return;
+    const int tiles = (op.n_inner + kTX - 1) / kTX;
+    const int outer = blockIdx.x / tiles;
+    const int c0 = (blockIdx.x % tiles) * kTX;
+    const int nl = min(kTX, op.n_inner - c0);
+    auto ld = [&](int line, int n) { return op.load(outer, n, c0 + line); };
+    auto st = [&](int line, int k, float2 v) { op.store(outer, k, c0 + line, v); };
+    block_fft<L, SIGN, true>(nl, ld, st, S, op.tw);
+}
+
+template <int L>
+static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, float* cg_r, CgState* cg) {
+    Workspace& w = P.ws;
+    const int N = P.N;
+    constexpr int ROWS = rows_per_block<L>();
+    const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
+    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
+    cudaError_t e;
+    // pass 1: rows of x (or p = r + beta p), forward, half spectrum
+    TRowsFwdOp a{{}, x, cg ? const_cast<float*>(x) : nullptr, cg_r, cg, w.t1, w.tw_2n, N * N, N};
+    if ((e = cudaFuncSetAttribute(k_rows_cg<L, TRowsFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+        return e;
+    k_rows_cg<L, TRowsFwdOp><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(a, cg);
+    // pass 2: y forward (N nonzero of 2N)
+    TColsYFwdOp b{w.t1, w.t2, w.tw_2n, N, N + 1, N};
+    if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, TColsYFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+        return e;
+    const int tiles_b = (N + 1 + kTX - 1) / kTX;
+    k_cols_cg<L, -1, TColsYFwdOp><<<N * tiles_b, kThreads, smem_cols, P.stream>>>(b, cg);
+    // pass 3: z forward x K-hat x z inverse
+    const int n_inner = 2 * N * (N + 1);
+    if ((e = cudaFuncSetAttribute(k_toep_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols))) return e;
+    k_toep_z<L><<<(n_inner + kTX - 1) / kTX, kThreads, smem_cols, P.stream>>>(w.t2, w.khat, w.tw_2n, n_inner, N, cg);
+    // pass 4: y inverse, keep y < N
+    TColsYInvOp d{w.t2, w.t1, w.tw_2n, N, N + 1, N};
+    if ((e = cudaFuncSetAttribute(k_cols_cg<L, +1, TColsYInvOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+        return e;
+    k_cols_cg<L, +1, TColsYInvOp><<<N * tiles_b, kThreads, smem_cols, P.stream>>>(d, cg);
+    // pass 5: rows inverse (Hermitian), crop, scale, + lam x, <x, y>
+    const float scale = 1.0f / ((float)L * (float)L * (float)L);
+    TRowsInvOp f{w.t1, x, y, w.red_a, cg, w.tw_2n, N * N, N, scale, lam, nullptr};
+    if ((e = cudaFuncSetAttribute(k_toep_rows_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+        return e;
+    k_toep_rows_inv<L><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, float* cg_r, CgState* cg) {
+    FIRM_SWITCH_2N(2 * P.N, { return toeplitz_l<LL>(P, x, y, lam, cg_r, cg); });
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace firm

@@ -1,0 +1,143 @@
+// firm_internal.h -- plan state, workspace layout and kernel launchers shared by the
+// translation units of the CUDA library.  Not part of the public ABI (include/firm.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/firm.h"
+
+namespace firm {
+
+constexpr int kBrick = 16;            // spreading brick edge in fine-grid cells
+constexpr int kKbDeg = 9;             // degree of the per-tap window polynomials
+constexpr int kMaxW = 8;              // widest Kaiser-Bessel window supported
+constexpr int kChunk = 16384;         // most points one spreading work item takes
+constexpr int kMaxHist = 20001;       // residual history capacity (iterations + 1)
+constexpr int kRedSlots = 4096;       // per-block partial sums of a reduction
+
+// Window polynomials: tap l of a point with fractional tap offset u in [0,1) has
+// weight phi(u + l - W/2) = sum_j c[l][j] z^j, z = 2u - 1 (Horner in z).
+struct KbPoly {
+    float c[kMaxW][kKbDeg + 1];
+};
+
+// Per-image slice geometry: rows 0 and 1 of R_m (the in-plane axes u, v of the slice,
+// xi = w1 u + w2 v) split into float hi + lo parts so that positions on the fine
+// grid are formed to ~1e-7 cells.
+struct ImgGeom {
+    float uh[3], ul[3], vh[3], vl[3];
+};
+
+// CG state on the device (FP64 scalars; Section 3.3).
+struct CgState {
+    double rr;        // <r, z> of the current iterate (z = r unpreconditioned)
+    double pq;        // <p, A p>
+    double beta;      // next p = z + beta p
+    double bnorm;     // ||rhs||
+    double tol;       // rel_tol * ||rhs|| (0: none)
+    int it;           // iterations done
+    int max_iter;
+    int done;         // 1: stop (converged, max_iter or breakdown)
+    int status;       // firm_status of the solve
+    unsigned int ticket_a, ticket_b;   // last-block counters of the two reductions
+};
+
+struct Workspace {
+    // inputs staged from host memory
+    double* R = nullptr;
+    double* shifts = nullptr;
+    int32_t* gid = nullptr;
+    void* images = nullptr;
+    // tables
+    ImgGeom* geom = nullptr;
+    int32_t* htab = nullptr;        // half-disc (k1, k2) packed as k1 | k2 << 16
+    float* h2 = nullptr;            // [group][t] h^2 (t = 0 halved)
+    float* h1 = nullptr;            // [group][t] h
+    float2* tw_n = nullptr;         // exp(-2 pi i j / L) for L = N, 2N, 4N
+    float2* tw_2n = nullptr;
+    float2* tw_4n = nullptr;
+    float* dec_k = nullptr;         // deconvolution factors, Ker (2N) and A*b (N)
+    float* dec_r = nullptr;
+    // spreading
+    float2* samples = nullptr;      // [m][t] h b (t = 0 halved)
+    uint32_t* count = nullptr;      // per brick
+    uint32_t* cursor = nullptr;
+    uint32_t* payload = nullptr;    // point ids m * nH + t sorted by brick
+    int4* work = nullptr;           // (brick, start, count, -)
+    int* counters = nullptr;        // [0] work items, [1] work cursor, [2] error flag
+    double* grid = nullptr;         // fine grid, FP64 (real for Ker, complex for A*b)
+    float2* fx1 = nullptr;          // FFT intermediates
+    float2* fx2 = nullptr;
+    // results
+    float* ker = nullptr;           // Ker half box
+    float* khat = nullptr;          // K-hat half spectrum
+    float* rhs = nullptr;           // A*b
+    // CG
+    float* x = nullptr;
+    float* r = nullptr;
+    float* p = nullptr;
+    float* q = nullptr;
+    float2* t1 = nullptr;           // N x N x (N+1)
+    float2* t2 = nullptr;           // N x 2N x (N+1)
+    double* red_a = nullptr;        // partial sums
+    double* red_b = nullptr;
+    double* hist = nullptr;
+    CgState* cg = nullptr;
+    size_t total = 0;
+};
+
+struct Plan {
+    firm_params p{};
+    std::vector<firm_ctf_group> groups;
+    cudaStream_t stream = nullptr;
+    char* base = nullptr;
+    Workspace ws;
+    int N = 0, Gk = 0, Gr = 0, nH = 0, nK = 0, nbk = 0, nbr = 0, n_ctf = 1;
+    size_t max_work = 0;
+    KbPoly poly{};
+    double lam_eff = 0.0;
+    bool have_kernel = false, have_rhs = false;
+    bool timing = false;
+    double stage_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    int num_sms = 0;
+    // device pointers of the current call's inputs (caller's or staged copies)
+    const double* cur_R = nullptr;
+    const double* cur_shifts = nullptr;
+    const int32_t* cur_gid = nullptr;
+    const void* cur_images = nullptr;
+    std::vector<int32_t> htab_host;
+};
+
+// Workspace layout (also used by firm_workspace_size with base = nullptr).
+size_t layout_workspace(const firm_params& p, char* base, Workspace& ws);
+
+// Host-side tables (double precision, from the definitions).
+void kb_build(int W, double sigma, KbPoly& poly, double* beta_out);
+double kb_phihat(double u, int W, double beta);     // FT of the normalised window
+std::vector<int32_t> half_disc(int N);               // (k1, k2) packed, ordered as in firm.h
+double wavelength_A(double kV);
+double ctf_value(const firm_ctf_group& g, double r_invA);
+
+// ---- launchers (spread.cu) ----
+cudaError_t launch_geom(const double* R, int M, ImgGeom* geom, cudaStream_t s);
+cudaError_t launch_bin(Plan& P, int M, bool kernel_channel);
+cudaError_t launch_spread(Plan& P, int M, bool kernel_channel);
+
+// ---- launchers (fft_passes.cu) ----
+cudaError_t fft_init_constants();
+cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* shifts, const int32_t* gid);
+cudaError_t launch_ker_transform(Plan& P);     // grid -> Ker half box
+cudaError_t launch_khat(Plan& P);              // Ker -> K-hat
+cudaError_t launch_rhs_transform(Plan& P);     // grid -> A*b
+// Toeplitz apply y = Ker * x + lam x.  With cg != nullptr the first pass forms
+// p = r + beta p in place (x = p, r given) and the last pass reduces <p, y>.
+cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, float* cg_r, CgState* cg);
+
+// ---- launchers (cg.cu) ----
+cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_tol);
+cudaError_t launch_cg_update(Plan& P);
+
+}  // namespace firm

@@ -1,0 +1,70 @@
+"""A FIRM plan whose workspace is a torch CUDA tensor (argument marshalling only)."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class Reconstructor:
+    """Owns one firm_plan: workspace from torch's caching allocator, stream = torch's
+    current stream on `device`.  Methods forward to the C ABI of the same name."""
+
+    def __init__(self, N: int, M: int, groups=None, W: int = 7, lam: float = 0.0,
+                 lambda_mode: int = L.FIRM_LAMBDA_RELATIVE, img_dtype: int = L.FIRM_IMG_F32,
+                 device="cuda:0", stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the FIRM CUDA path needs a CUDA device")
+        self.device = torch.device(device)
+        table = np.zeros((0, 6)) if groups is None else np.asarray(groups, float).reshape(-1, 6)
+        self.params = L.make_params(N, M, table.shape[0], W, 2.0, lam, lambda_mode, 0, img_dtype, 0)
+        self._groups = L.make_groups(table)
+        self.ws_bytes = L.firm_workspace_size(self.params)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            base = self.workspace.data_ptr()
+            self._base = (base + 255) // 256 * 256
+            self.plan = L.firm_plan(self.params, self._groups, self._base, self.ws_bytes, self.stream.cuda_stream)
+        self.N, self.M = N, M
+
+    # -- FIRM steps --------------------------------------------------------------
+    def kernel(self, R, group=None, khat_out=None, M=None):
+        L.firm_kernel(self.plan, self.M if M is None else M, R, group, khat_out)
+
+    def backproject(self, images, shifts, R, group=None, rhs_out=None, M=None):
+        L.firm_backproject(self.plan, self.M if M is None else M, images, shifts, R, group, rhs_out)
+
+    def cg_solve(self, x, max_iter, rel_tol=0.0, rhs=None, resid_hist=None, allow=()):
+        return L.firm_cg_solve(self.plan, rhs, x, max_iter, rel_tol, resid_hist, allow)
+
+    def toeplitz_apply(self, x, y):
+        L.firm_toeplitz_apply(self.plan, x, y)
+
+    def lambda_eff(self) -> float:
+        return L.firm_lambda_eff(self.plan)
+
+    def copy_out(self, which, dst):
+        L.firm_copy_out(self.plan, which, dst)
+
+    def set_timing(self, on=True):
+        L.firm_set_timing(self.plan, on)
+
+    def stage_times(self):
+        return L.firm_stage_times(self.plan)
+
+    # -- buffers ---------------------------------------------------------------------
+    def half_shape(self):
+        return (2 * self.N, 2 * self.N, self.N + 1)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            L.firm_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
