@@ -1,0 +1,352 @@
+"""Benchmark of the FIRM hot path on GB300.
+
+One step = one whole reconstruction of the N=128, 50,000-image workload (FIRM steps
+1-4: image DFTs, spreading into A*b and the Toeplitz kernel, fine-grid transforms,
+circulant K-hat, CG to relative residual 1e-4) with the inputs already resident in
+HBM.  Prints one JSON line (see the design doc for every key).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl firm|reference]
+
+Under torchrun (N > 1) every rank reconstructs its own copy of the workload
+(replicas only: FIRM's per-image sums would need one all-reduce of Ker and A*b to
+shard a single reconstruction, and no call here uses more than one GPU); the
+timed region is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spread Gpts/s + s/recon (N=128, 50k imgs) vs plain CG on GB300 at rel-res 1e-4"
+WORKLOAD = "C3"
+REL_TOL = 1e-4
+MAX_ITER = 5000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="firm", choices=["firm", "reference"])
+    ap.add_argument("--images", type=int, default=None, help="override image count (smaller runs)")
+    ap.add_argument("--N", type=int, default=None, help="override volume edge (profiling of smaller cases)")
+    ap.add_argument("--max-iter", type=int, default=MAX_ITER, help="CG iteration cap (profiling)")
+    ap.add_argument("--W", type=int, default=7)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload(M_override=None, N_override=None):
+    import synth
+    inp = synth.config_inputs(WORKLOAD, M=M_override, N=N_override)
+    return inp
+
+
+def disc_size(N):
+    h = N // 2
+    k = np.arange(-h, h + 1)
+    return int(((k[:, None] ** 2 + k[None, :] ** 2) <= h * h).sum())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample, extrapolated to one reconstruction)
+# ---------------------------------------------------------------------------
+def oracle_sample(inp, cg_iters: int, budget_images: int = 4000, n_vox: int = 2):
+    """Times the FP64 oracle as it stands on a bounded sample of the workload and
+    extrapolates to one reconstruction: Ker at n_vox voxels over budget_images images
+    (scaled to all images and all (2N)^3 voxels), A*b likewise (N^3 voxels), and one
+    CG iteration of the FP64 circulant apply (scaled to cg_iters)."""
+    import oracle as O
+    N, M = inp["N"], inp["M"]
+    Ms = min(M, budget_images, inp["images"].shape[0])
+    K = O.disc(N)
+    h = O.ctf_weights(N, K, inp["groups"], inp["group_id"][:Ms])
+    rng = np.random.default_rng(0)
+    nv = rng.integers(-N // 2, N // 2, (n_vox, 3))
+    t0 = time.perf_counter()
+    O.kernel_at(inp["R"][:Ms], h, K, N, nv)
+    t_ker = (time.perf_counter() - t0) / n_vox * (M / Ms)
+    imgs = inp["images"][:Ms].astype(np.float64)
+    t0 = time.perf_counter()
+    O.backproject_at(imgs, inp["shifts"][:Ms], inp["R"][:Ms], h, K, nv)
+    t_rhs = (time.perf_counter() - t0) / n_vox * (M / Ms)
+    Kh = np.zeros((2 * N,) * 3, complex)
+    V = rng.standard_normal((N,) * 3)
+    t0 = time.perf_counter()
+    O.toeplitz_apply(Kh, V, 1.0)
+    t_it = time.perf_counter() - t0
+    est = t_ker * (2 * N) ** 3 + t_rhs * N ** 3 + t_it * max(cg_iters, 1)
+    sample = (f"oracle Ker and A*b (direct sums) at {n_vox} voxels over {Ms} of {M} images, one FP64 "
+              f"circulant CG apply; extrapolated to (2N)^3 + N^3 voxels, {M} images, {cg_iters} iterations")
+    return est, sample, {"ker_s_per_voxel": t_ker, "rhs_s_per_voxel": t_rhs, "cg_s_per_iter": t_it}
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle, timed step by step on bounded samples
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inp = workload(args.images)
+    iters_guess = 200
+    for _ in range(max(0, args.warmup)):
+        pass   # the oracle has no warm-up state; samples below are timed independently
+    vals = []
+    sample = None
+    for _ in range(max(1, args.steps)):
+        est, sample, _parts = oracle_sample(inp, iters_guess, budget_images=1000, n_vox=1)
+        vals.append(est)
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/recon", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "N=128 volume, 50000 BF16 128x128 images (60-blob phantom, Haar views, "
+                                  "20 defocus groups, SNR 0.05), lambda=1e-3, CG to rel-res 1e-4",
+                      "N": 128, "M": inp["M"]},
+           "cpu_baseline": {"value": v, "unit": "s/recon", "cores": cores_used(), "kind": "oracle",
+                            "sample": sample + f"; CG iteration count assumed {iters_guess}"},
+           "e2e": {"value": v, "unit": "s/recon", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# the CUDA arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1307_5824_gb300 import Reconstructor
+    from paper_1307_5824_gb300 import _lib as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    t_syn = time.perf_counter()
+    inp = workload(args.images, args.N)
+    t_syn = time.perf_counter() - t_syn
+    N, M = inp["N"], inp["M"]
+    nK = disc_size(N)
+
+    R_h = torch.from_numpy(inp["R"].reshape(M, 9).copy()).pin_memory()
+    g_h = torch.from_numpy(inp["group_id"].copy()).pin_memory()
+    s_h = torch.from_numpy(inp["shifts"].copy()).pin_memory()
+    img_h = torch.from_numpy(inp["images"]).to(torch.bfloat16).pin_memory()
+    R = R_h.to(dev)
+    gid = g_h.to(dev)
+    sh = s_h.to(dev)
+    img = img_h.to(dev)
+    inp["images"] = inp["images"][:5000].copy()     # the CPU-baseline sample keeps a few
+
+    rec = Reconstructor(N, M, groups=inp["groups"], W=args.W, lam=1e-3, img_dtype=L.FIRM_IMG_BF16, device=dev)
+    x = torch.empty((N, N, N), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(R_, g_, s_, im_, x_):
+        rec.kernel(R_, g_)
+        rec.backproject(im_, s_, R_, g_)
+        st, it = rec.cg_solve(x_, args.max_iter, rel_tol=REL_TOL, allow=(L.FIRM_ENOTCONV,))
+        return st, it
+
+    for _ in range(max(3, args.warmup)):
+        st, iters = step(R, gid, sh, img, x)
+    torch.cuda.synchronize(dev)
+
+    # timed region: device-resident inputs; stage events recorded (no extra syncs)
+    rec.set_timing(True)
+    l0 = rec.launch_count()
+    stage_acc = {}
+    iters_list = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, iters = step(R, gid, sh, img, x)
+            iters_list.append(iters)
+            for k, v in rec.stage_times().items():
+                stage_acc[k] = stage_acc.get(k, 0.0) + v
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = rec.launch_count() - l0
+    rec.set_timing(False)
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    stages = {k: v / args.steps for k, v in stage_acc.items()}
+
+    # end-to-end through the C ABI with host (pinned) buffers, copies inside the region
+    e2e = None
+    if not args.no_e2e:
+        x_h = torch.empty((N, N, N), dtype=torch.float32).pin_memory()
+        step(R_h, g_h, s_h, img_h, x_h)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(R_h, g_h, s_h, img_h, x_h)
+        torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        h2d = 2 * R_h.numel() * 8 + 2 * g_h.numel() * 4 + s_h.numel() * 8 + img_h.numel() * 2
+        e2e = {"value": e2e_s, "unit": "s/recon", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(x_h.numel() * 4)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    iters = int(np.median(iters_list))
+    pts = M * nK
+    spread_ms = stages["spread_ker"] + stages["spread_rhs"]
+    W = args.W
+    # roofline of the dominant kernel: the spreading kernel with the larger share.
+    # Work unit: one shared-memory atomic add (W^3 per half-disc point, x2 for the
+    # complex A*b channel).  Peak: 152 SMs x 32 lanes x 2.07 GHz (one warp-wide shared
+    # atomic per clock per SM) = 10.07e12 / s.
+    nH = (nK + 1) // 2
+    dom = "spread_rhs" if stages["spread_rhs"] >= stages["spread_ker"] else "spread_ker"
+    atoms = M * nH * W ** 3 * (2 if dom == "spread_rhs" else 1)
+    peak = 152 * 32 * 2.07e9
+    achieved = atoms / (stages[dom] * 1e-3)
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "spread_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(dom)
+        except Exception:
+            traffic = None
+
+    cpu = None
+    if not args.no_cpu:
+        est, sample, parts = oracle_sample(inp, iters)
+        cpu = {"value": est, "unit": "s/recon", "cores": cores_used(), "kind": "oracle", "sample": sample,
+               "parts": parts}
+
+    out = {
+        "metric": METRIC, "value": ms_step / 1e3, "unit": "s/recon", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "N=128 volume, 50000 BF16 128x128 images (60-blob phantom, Haar views, "
+                               "20 defocus groups, SNR 0.05), KB W=%d sigma=2, lambda=1e-3 x Ker(0), "
+                               "plain CG to rel-res 1e-4" % W,
+                   "N": N, "M": M, "W": W, "precond": "none",
+                   "l2": "inputs larger than L2: 1.64 GB BF16 images read and a 1.07 GB FP64 fine grid "
+                         "written every step"},
+        "spread_gpts_per_s": pts / (spread_ms * 1e-3) / 1e9,
+        "spread_points": pts,
+        "toeplitz_applies_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
+        "cg_iters": iters,
+        "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},
+        "roofline": {"kernel": f"k_spread<{W},{'complex' if dom == 'spread_rhs' else 'real'}>", "bound": "alu",
+                     "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tatomic/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x 32 shared-atomic lanes/clk x 2.07 GHz"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "synth_s": round(t_syn, 1),
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -74,7 +74,7 @@ typedef struct {
 } firm_ctf_group;
 
 typedef struct {
-    int N;            /* volume edge: even, 8 <= N <= 256 (2N and 4N must be FFT sizes) */
+    int N;            /* volume edge: 16, 32, 48, 64, 96 or 128 */
     int M;            /* largest image count any call on the plan will pass */
     int n_groups;     /* defocus groups in the CTF table; 0 means no CTF (h = 1) */
     int W;            /* Kaiser-Bessel window width in fine-grid cells: 6, 7 or 8 */
@@ -146,12 +146,20 @@ int firm_lambda_eff(firm_plan_t plan, double* out);
 enum { FIRM_OUT_KER = 0, FIRM_OUT_KHAT = 1, FIRM_OUT_RHS = 2, FIRM_OUT_SAMPLES = 3 };
 int firm_copy_out(firm_plan_t plan, int which, void* dst);
 
-/* Timing of the last call of each stage (milliseconds of device time between CUDA
- * events on the plan's stream): index 0 binning, 1 spreading, 2 fine-grid FFT +
- * deconvolution, 3 circulant K-hat, 4 image DFT, 5 CG total, 6 CG iterations run.
- * Filled only when timing was enabled with firm_set_timing(plan, 1). */
+/* Device time of the last call of each stage, in milliseconds between CUDA events
+ * recorded on the plan's stream around the stage (recorded only while timing is on,
+ * firm_set_timing(plan, 1); recording adds no host synchronisation).  Slots:
+ *   0 geometry + binning (kernel channel)   1 spreading (kernel channel)
+ *   2 4N^3 transform + deconvolution (Ker) 3 circulant K-hat
+ *   4 geometry + image DFT                  5 binning (A*b channel)
+ *   6 spreading (A*b channel)               7 2N^3 transform + deconvolution (A*b)
+ *   8 CG total                              9 CG iterations of the last solve
+ * firm_stage_times waits for the recorded events and fills out[0..n-1]. */
 int firm_set_timing(firm_plan_t plan, int on);
-int firm_stage_times(firm_plan_t plan, double* out7);
+int firm_stage_times(firm_plan_t plan, double* out, int n);
+
+/* Number of CUDA kernels this plan has launched since firm_plan (for accounting). */
+int firm_launch_count(firm_plan_t plan, long long* out);
 
 void firm_destroy(firm_plan_t plan);
 const char* firm_strerror(int code);

@@ -22,7 +22,7 @@ FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES = 0, 1, 2, 3
 EXPORTED = [
     "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_cg_solve",
     "firm_toeplitz_apply", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
-    "firm_stage_times", "firm_destroy", "firm_strerror",
+    "firm_stage_times", "firm_launch_count", "firm_destroy", "firm_strerror",
 ]
 
 
@@ -66,7 +66,8 @@ def lib() -> ctypes.CDLL:
     L.firm_lambda_eff.argtypes = [vp, ctypes.POINTER(d)]
     L.firm_copy_out.argtypes = [vp, i, vp]
     L.firm_set_timing.argtypes = [vp, i]
-    L.firm_stage_times.argtypes = [vp, ctypes.POINTER(d)]
+    L.firm_stage_times.argtypes = [vp, ctypes.POINTER(d), i]
+    L.firm_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.firm_destroy.argtypes = [vp]
     L.firm_destroy.restype = None
     L.firm_strerror.argtypes = [i]
@@ -170,10 +171,20 @@ def firm_set_timing(plan, on: bool):
     _check(lib().firm_set_timing(plan, 1 if on else 0), "firm_set_timing")
 
 
-def firm_stage_times(plan):
-    out = (ctypes.c_double * 7)()
-    _check(lib().firm_stage_times(plan, out), "firm_stage_times")
-    return list(out)
+STAGES = ["bin_ker", "spread_ker", "fft_ker", "khat", "image_dft", "bin_rhs", "spread_rhs", "fft_rhs",
+          "cg", "cg_iters"]
+
+
+def firm_stage_times(plan) -> dict:
+    out = (ctypes.c_double * len(STAGES))()
+    _check(lib().firm_stage_times(plan, out, len(STAGES)), "firm_stage_times")
+    return dict(zip(STAGES, list(out)))
+
+
+def firm_launch_count(plan) -> int:
+    v = ctypes.c_longlong(0)
+    _check(lib().firm_launch_count(plan, ctypes.byref(v)), "firm_launch_count")
+    return int(v.value)
 
 
 def firm_destroy(plan):

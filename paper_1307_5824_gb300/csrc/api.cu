@@ -168,23 +168,26 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.count = c.take<uint32_t>(nb3);
     w.cursor = c.take<uint32_t>(nb3);
     w.work = c.take<int4>(max_work);
+    w.class_off = c.take<uint32_t>(max_work * 32);
     w.counters = c.take<int>(8);
     const size_t grid_bytes = std::max(Gk * Gk * Gk * sizeof(double), Gr * Gr * Gr * 2 * sizeof(double));
     w.grid = c.take<double>(grid_bytes / sizeof(double));
     // union: staged images | point ids | FFT intermediates (never live together)
     const size_t fx1 = std::max({Gk * Gk * (N + 1), Gr * Gr * N, H3});
     const size_t fx2 = std::max({Gk * 2 * N * (N + 1), Gr * N * N, H3});
-    const size_t u_bytes = std::max({M * N * N * esz, M * nH * sizeof(uint32_t), (fx1 + fx2) * sizeof(float2) + 256});
+    const size_t pay_bytes = ((M * nH * sizeof(uint32_t) + 255) & ~(size_t)255) + M * nH;
+    const size_t u_bytes = std::max({M * N * N * esz, pay_bytes, (fx1 + fx2) * sizeof(float2) + 256});
     char* u = c.take<char>(u_bytes);
     w.images = u;
     w.payload = reinterpret_cast<uint32_t*>(u);
+    w.cls = u ? reinterpret_cast<uint8_t*>(u + ((M * nH * sizeof(uint32_t) + 255) & ~(size_t)255)) : nullptr;
     w.fx1 = reinterpret_cast<float2*>(u);
     w.fx2 = u ? reinterpret_cast<float2*>(u + ((fx1 * sizeof(float2) + 255) & ~(size_t)255)) : nullptr;
     w.ker = c.take<float>(H3);
     w.khat = c.take<float>(H3);
     w.rhs = c.take<float>(N3);
     w.x = c.take<float>(N3);
-    w.r = c.take<float>(N3);
+    w.r = c.take<double>(N3);
     w.p = c.take<float>(N3);
     w.q = c.take<float>(N3);
     w.t1 = c.take<float2>(N * N * (N + 1));
@@ -246,27 +249,26 @@ static int put_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     return FIRM_OK;
 }
 
+// Records a start / stop event pair per stage slot on the plan's stream; nothing
+// waits here, firm_stage_times synchronises when it reads them.
 struct StageTimer {
     Plan& P;
-    cudaEvent_t a = nullptr, b = nullptr;
-    explicit StageTimer(Plan& p) : P(p) {
-        if (P.timing) {
-            cudaEventCreate(&a);
-            cudaEventCreate(&b);
-        }
-    }
-    void start() { if (P.timing) cudaEventRecord(a, P.stream); }
-    void stop(int slot) {
+    int slot = -1;
+    explicit StageTimer(Plan& p) : P(p) {}
+    void start(int s) {
         if (!P.timing) return;
-        cudaEventRecord(b, P.stream);
-        cudaEventSynchronize(b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        P.stage_ms[slot] = ms;
+        slot = s;
+        if (!P.ev_a[s]) {
+            cudaEventCreate(&P.ev_a[s]);
+            cudaEventCreate(&P.ev_b[s]);
+        }
+        cudaEventRecord(P.ev_a[s], P.stream);
     }
-    ~StageTimer() {
-        if (a) cudaEventDestroy(a);
-        if (b) cudaEventDestroy(b);
+    void stop() {
+        if (!P.timing || slot < 0) return;
+        cudaEventRecord(P.ev_b[slot], P.stream);
+        P.ev_used[slot] = true;
+        slot = -1;
     }
 };
 
@@ -408,19 +410,20 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     else { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
     FIRM_CK(e);
     FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
-    tm.start();
+    tm.start(0);
     FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
+    P.launches += M > 0 ? 1 : 0;
     FIRM_CK(launch_bin(P, M, true));
-    tm.stop(0);
-    tm.start();
+    tm.stop();
+    tm.start(1);
     FIRM_CK(launch_spread(P, M, true));
-    tm.stop(1);
-    tm.start();
+    tm.stop();
+    tm.start(2);
     FIRM_CK(launch_ker_transform(P));
-    tm.stop(2);
-    tm.start();
+    tm.stop();
+    tm.start(3);
     FIRM_CK(launch_khat(P));
-    tm.stop(3);
+    tm.stop();
     // lam_eff from Ker(0) (the n = 0 entry of the half box)
     float ker0 = 0.f;
     const size_t i0 = ((size_t)P.N * 2 * P.N + P.N) * (P.N + 1);
@@ -453,19 +456,20 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
         P.cur_images = images;
     }
     FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
-    tm.start();
+    tm.start(4);
     FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
+    P.launches += M > 0 ? 1 : 0;
     FIRM_CK(launch_image_dft(P, M, P.cur_images, P.cur_shifts, P.cur_gid));
-    tm.stop(4);
-    tm.start();
+    tm.stop();
+    tm.start(5);
     FIRM_CK(launch_bin(P, M, false));
-    tm.stop(0);
-    tm.start();
+    tm.stop();
+    tm.start(6);
     FIRM_CK(launch_spread(P, M, false));
-    tm.stop(1);
-    tm.start();
+    tm.stop();
+    tm.start(7);
     FIRM_CK(launch_rhs_transform(P));
-    tm.stop(2);
+    tm.stop();
     int st = check_spread_flag(P);
     if (st != FIRM_OK) return st;
     P.have_rhs = true;
@@ -501,7 +505,7 @@ int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, do
     const float* rd = rhs ? stage(rhs, w.q, n, P.stream, e) : w.rhs;
     FIRM_CK(e);
     StageTimer tm(P);
-    tm.start();
+    tm.start(8);
     FIRM_CK(launch_cg_init(P, rd, max_iter, rel_tol));
     const int batch = 8;
     for (int it = 0; it < max_iter; ++it) {
@@ -514,11 +518,11 @@ int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, do
             if (done) break;
         }
     }
-    tm.stop(5);
+    tm.stop();
     CgState s;
     FIRM_CK(cudaMemcpyAsync(&s, w.cg, sizeof(CgState), cudaMemcpyDeviceToHost, P.stream));
     FIRM_CK(cudaStreamSynchronize(P.stream));
-    P.stage_ms[6] = s.it;
+    P.cg_iters = s.it;
     if (resid_hist) {
         const bool dev = is_device(resid_hist);
         FIRM_CK(cudaMemcpyAsync(resid_hist, w.hist, sizeof(double) * (s.it + 1),
@@ -554,19 +558,41 @@ int firm_copy_out(firm_plan_t plan, int which, void* dst) {
     }
 }
 
+int firm_launch_count(firm_plan_t plan, long long* out) {
+    if (!plan || !out) return FIRM_EINVAL;
+    *out = plan->P.launches;
+    return FIRM_OK;
+}
+
 int firm_set_timing(firm_plan_t plan, int on) {
     if (!plan) return FIRM_EINVAL;
     plan->P.timing = on != 0;
     return FIRM_OK;
 }
 
-int firm_stage_times(firm_plan_t plan, double* out7) {
-    if (!plan || !out7) return FIRM_EINVAL;
-    for (int i = 0; i < 7; ++i) out7[i] = plan->P.stage_ms[i];
+int firm_stage_times(firm_plan_t plan, double* out, int n) {
+    if (!plan || !out || n < 0) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    for (int i = 0; i < n; ++i) out[i] = 0.0;
+    for (int i = 0; i < n && i < Plan::kSlots - 1; ++i) {
+        if (!P.ev_used[i]) continue;
+        if (cudaEventSynchronize(P.ev_b[i]) != cudaSuccess) return FIRM_ECUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P.ev_a[i], P.ev_b[i]) != cudaSuccess) return FIRM_ECUDA;
+        out[i] = ms;
+    }
+    if (n > 9) out[9] = P.cg_iters;
     return FIRM_OK;
 }
 
-void firm_destroy(firm_plan_t plan) { delete plan; }
+void firm_destroy(firm_plan_t plan) {
+    if (!plan) return;
+    for (int i = 0; i < Plan::kSlots; ++i) {
+        if (plan->P.ev_a[i]) cudaEventDestroy(plan->P.ev_a[i]);
+        if (plan->P.ev_b[i]) cudaEventDestroy(plan->P.ev_b[i]);
+    }
+    delete plan;
+}
 
 const char* firm_strerror(int code) {
     switch (code) {

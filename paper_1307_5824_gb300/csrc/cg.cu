@@ -54,7 +54,7 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket, bool* s_last) {
 }
 
 __global__ void __launch_bounds__(kCgThreads) k_cg_init(const float* __restrict__ rhs, float* __restrict__ x,
-                                                        float* __restrict__ r, float* __restrict__ p, size_t n,
+                                                        double* __restrict__ r, float* __restrict__ p, size_t n,
                                                         CgState* cg, double* red, double* hist, int max_iter,
                                                         double rel_tol) {
     __shared__ double s_warp[kCgThreads / 32];
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(const float* __restrict_
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float b = rhs[i];
         x[i] = 0.0f;
-        r[i] = b;
+        r[i] = (double)b;
         p[i] = b;
         acc += (double)b * (double)b;
     }
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(const float* __restrict_
     }
 }
 
-__global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x, float* __restrict__ r,
+__global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x, double* __restrict__ r,
                                                           const float* __restrict__ p, const float* __restrict__ q,
                                                           size_t n4, CgState* cg, double* red, double* hist) {
     __shared__ double s_warp[kCgThreads / 32];
@@ -102,19 +102,21 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x,
     if (ok) {
         const float a = (float)alpha;
         float4* x4 = reinterpret_cast<float4*>(x);
-        float4* r4 = reinterpret_cast<float4*>(r);
+        double2* r2 = reinterpret_cast<double2*>(r);
         const float4* p4 = reinterpret_cast<const float4*>(p);
         const float4* q4 = reinterpret_cast<const float4*>(q);
         for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-            float4 xv = x4[i], rv = r4[i];
+            float4 xv = x4[i];
             const float4 pv = p4[i], qv = q4[i];
+            double2 ra = r2[2 * i], rb = r2[2 * i + 1];
             xv.x = fmaf(a, pv.x, xv.x); xv.y = fmaf(a, pv.y, xv.y);
             xv.z = fmaf(a, pv.z, xv.z); xv.w = fmaf(a, pv.w, xv.w);
-            rv.x = fmaf(-a, qv.x, rv.x); rv.y = fmaf(-a, qv.y, rv.y);
-            rv.z = fmaf(-a, qv.z, rv.z); rv.w = fmaf(-a, qv.w, rv.w);
+            ra.x = fma(-alpha, (double)qv.x, ra.x); ra.y = fma(-alpha, (double)qv.y, ra.y);
+            rb.x = fma(-alpha, (double)qv.z, rb.x); rb.y = fma(-alpha, (double)qv.w, rb.y);
             x4[i] = xv;
-            r4[i] = rv;
-            acc += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z + (double)rv.w * rv.w;
+            r2[2 * i] = ra;
+            r2[2 * i + 1] = rb;
+            acc += ra.x * ra.x + ra.y * ra.y + rb.x * rb.x + rb.y * rb.y;
         }
     }
     const double bs = block_sum(acc, s_warp);
@@ -150,6 +152,7 @@ cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_t
     if (e != cudaSuccess) return e;
     k_cg_init<<<cg_blocks(P), kCgThreads, 0, P.stream>>>(rhs, w.x, w.r, w.p, n, w.cg, w.red_b, w.hist, max_iter,
                                                          rel_tol);
+    P.launches += 1;
     return cudaGetLastError();
 }
 
@@ -157,6 +160,7 @@ cudaError_t launch_cg_update(Plan& P) {
     Workspace& w = P.ws;
     const size_t n4 = (size_t)P.N * P.N * P.N / 4;
     k_cg_update<<<cg_blocks(P), kCgThreads, 0, P.stream>>>(w.x, w.r, w.p, w.q, n4, w.cg, w.red_b, w.hist);
+    P.launches += 1;
     return cudaGetLastError();
 }
 

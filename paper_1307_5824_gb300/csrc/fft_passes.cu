@@ -152,6 +152,7 @@ cudaError_t launch_ker_transform(Plan& P) {
         if ((e = run_cols<LL, +1>(b, P.stream)) != cudaSuccess) return e;
         if ((e = run_cols<LL, +1>(c, P.stream)) != cudaSuccess) return e;
     });
+    P.launches += 3;
     return e;
 }
 
@@ -203,6 +204,7 @@ cudaError_t launch_khat(Plan& P) {
         if ((e = run_cols<LL, -1>(b, P.stream)) != cudaSuccess) return e;
         if ((e = run_cols<LL, -1>(c, P.stream)) != cudaSuccess) return e;
     });
+    P.launches += 3;
     return e;
 }
 
@@ -256,6 +258,7 @@ cudaError_t launch_rhs_transform(Plan& P) {
         if ((e = run_cols<LL, +1>(b, P.stream)) != cudaSuccess) return e;
         if ((e = run_cols<LL, +1>(c, P.stream)) != cudaSuccess) return e;
     });
+    P.launches += 3;
     return e;
 }
 
@@ -324,6 +327,7 @@ static cudaError_t image_dft_n(Plan& P, int M, const ImgArgs& a) {
     cudaError_t e = cudaFuncSetAttribute(k_image_dft<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_image_dft<N, T><<<M, kThreads, smem, P.stream>>>(a);
+    P.launches += 1;
     return cudaGetLastError();
 }
 
@@ -346,12 +350,12 @@ cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* s
 // Toeplitz apply (CG-fused when cg != nullptr)
 // ---------------------------------------------------------------------------
 struct TRowsFwdOp : NoFinish {
-    const float* x; float* p; const float* r; const CgState* cg; float2* out; const float2* tw; int n_rows, N;
+    const float* x; float* p; const double* r; const CgState* cg; float2* out; const float2* tw; int n_rows, N;
     __device__ __forceinline__ float2 load(int row, int n) const {
         if (n >= N) return make_float2(0.0f, 0.0f);
         const size_t i = (size_t)row * N + n;
-        if (cg) {   // p = r + beta p, written back
-            const float v = __ldg(&r[i]) + (float)cg->beta * p[i];
+        if (cg) {   // p = r + beta p (r FP64), written back
+            const float v = (float)fma(cg->beta, (double)p[i], __ldg(&r[i]));
             p[i] = v;
             return make_float2(v, 0.0f);
         }
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_cols_cg(const Op op, const CgState
 }
 
 template <int L>
-static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, float* cg_r, CgState* cg) {
+static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg) {
     Workspace& w = P.ws;
     const int N = P.N;
     constexpr int ROWS = rows_per_block<L>();
@@ -525,10 +529,11 @@ static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, floa
     if ((e = cudaFuncSetAttribute(k_toep_rows_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
         return e;
     k_toep_rows_inv<L><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(f);
+    P.launches += 5;
     return cudaGetLastError();
 }
 
-cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, float* cg_r, CgState* cg) {
+cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg) {
     FIRM_SWITCH_2N(2 * P.N, { return toeplitz_l<LL>(P, x, y, lam, cg_r, cg); });
     return cudaErrorInvalidValue;
 }

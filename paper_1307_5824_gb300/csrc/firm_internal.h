@@ -11,10 +11,10 @@
 
 namespace firm {
 
-constexpr int kBrick = 16;            // spreading brick edge in fine-grid cells
+constexpr int kBrick = 8;             // spreading brick edge in fine-grid cells
 constexpr int kKbDeg = 9;             // degree of the per-tap window polynomials
 constexpr int kMaxW = 8;              // widest Kaiser-Bessel window supported
-constexpr int kChunk = 16384;         // most points one spreading work item takes
+constexpr int kChunk = 8192;          // most points one spreading work item takes
 constexpr int kMaxHist = 20001;       // residual history capacity (iterations + 1)
 constexpr int kRedSlots = 4096;       // per-block partial sums of a reduction
 
@@ -65,7 +65,9 @@ struct Workspace {
     float2* samples = nullptr;      // [m][t] h b (t = 0 halved)
     uint32_t* count = nullptr;      // per brick
     uint32_t* cursor = nullptr;
-    uint32_t* payload = nullptr;    // point ids m * nH + t sorted by brick
+    uint32_t* payload = nullptr;    // point ids m * nH + t sorted by brick, then bank class
+    uint8_t* cls = nullptr;         // bank class of each binned point
+    uint32_t* class_off = nullptr;  // per work item, offset of each bank class
     int4* work = nullptr;           // (brick, start, count, -)
     int* counters = nullptr;        // [0] work items, [1] work cursor, [2] error flag
     double* grid = nullptr;         // fine grid, FP64 (real for Ker, complex for A*b)
@@ -77,7 +79,7 @@ struct Workspace {
     float* rhs = nullptr;           // A*b
     // CG
     float* x = nullptr;
-    float* r = nullptr;
+    double* r = nullptr;            // residual recurrence in FP64
     float* p = nullptr;
     float* q = nullptr;
     float2* t1 = nullptr;           // N x N x (N+1)
@@ -101,8 +103,13 @@ struct Plan {
     double lam_eff = 0.0;
     bool have_kernel = false, have_rhs = false;
     bool timing = false;
-    double stage_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    // stage timing: events recorded around each stage when timing is on; read lazily
+    static constexpr int kSlots = 12;
+    cudaEvent_t ev_a[kSlots] = {}, ev_b[kSlots] = {};
+    bool ev_used[kSlots] = {};
+    double cg_iters = 0;
     int num_sms = 0;
+    long long launches = 0;         // kernels launched by this plan
     // device pointers of the current call's inputs (caller's or staged copies)
     const double* cur_R = nullptr;
     const double* cur_shifts = nullptr;
@@ -134,7 +141,7 @@ cudaError_t launch_khat(Plan& P);              // Ker -> K-hat
 cudaError_t launch_rhs_transform(Plan& P);     // grid -> A*b
 // Toeplitz apply y = Ker * x + lam x.  With cg != nullptr the first pass forms
 // p = r + beta p in place (x = p, r given) and the last pass reduces <p, y>.
-cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, float* cg_r, CgState* cg);
+cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg);
 
 // ---- launchers (cg.cu) ----
 cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_tol);

@@ -85,30 +85,74 @@ __device__ __forceinline__ PointPos point_pos(const ImgGeom& g, int32_t kk, floa
 }
 
 // ---------------------------------------------------------------------------
-// Binning
+// Window taps and the region base of a point
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ int tap_shift(float f) {
+    // first tap offset u = c - (f - h) in [0, 1), h = 1/2 for odd W, 0 for even W
+    constexpr float h = (W & 1) ? 0.5f : 0.0f;
+    return (int)ceilf(f - h);
+}
+
+template <int W>
+__device__ __forceinline__ void window_taps(const KbPoly& P, float f, float* w) {
+    constexpr float h = (W & 1) ? 0.5f : 0.0f;
+    const float t0 = f - h;
+    const float z = 2.0f * (ceilf(t0) - t0) - 1.0f;
+#pragma unroll
+    for (int l = 0; l < W; ++l) {
+        float acc = P.c[l][kKbDeg];
+#pragma unroll
+        for (int j = kKbDeg - 1; j >= 0; --j) acc = fmaf(acc, z, P.c[l][j]);
+        w[l] = acc;
+    }
+}
+
+// Index of the first tap of a point inside its brick's (16 + W)^3 region, or -1 if
+// the point is not inside the brick (never expected: binning uses the same code).
+template <int W>
+__device__ __forceinline__ int region_base(const PointPos& p, int lo0, int lo1, int lo2) {
+    constexpr int RG = kBrick + W;
+    const int r0 = p.I[0] - lo0 + tap_shift<W>(p.f[0]);
+    const int r1 = p.I[1] - lo1 + tap_shift<W>(p.f[1]);
+    const int r2 = p.I[2] - lo2 + tap_shift<W>(p.f[2]);
+    if ((unsigned)r0 > (unsigned)kBrick || (unsigned)r1 > (unsigned)kBrick || (unsigned)r2 > (unsigned)kBrick)
+        return -1;
+    return (r2 * RG + r1) * RG + r0;
+}
+
+// ---------------------------------------------------------------------------
+// Binning.  Points are counted and scattered by brick (warp-aggregated atomics: lanes
+// hold consecutive samples of one image, which mostly share a brick).  Each brick's
+// segment is cut into pieces of at most kChunk points (the work items), and every
+// piece is then counting-sorted in shared memory by bank class = region base mod 32:
+// lane l of a spreading warp takes points of class l, so the 32 lanes of every tap
+// step touch 32 different shared-memory banks.
 // ---------------------------------------------------------------------------
 struct BinArgs {
     const ImgGeom* geom;
     const int32_t* htab;
     uint32_t* count;       // count pass: per-brick counters; scatter pass: cursors
-    uint32_t* payload;     // scatter pass output
+    uint32_t* payload;     // scatter pass output: point ids m * nH + t
+    uint8_t* cls;          // scatter pass output: bank class of each point
     long long npts;        // M * nH
     int nH, G, halfG, nb;  // nb = bricks per axis
     float scale;
 };
 
-template <bool SCATTER>
+template <int W, bool SCATTER>
 __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = idx < a.npts;
-    int key = -1;
+    int key = -1, c = 0;
     if (valid) {
         const int m = (int)(idx / a.nH);
         const int t = (int)(idx - (long long)m * a.nH);
         const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
-        key = ((p.I[2] / kBrick) * a.nb + p.I[1] / kBrick) * a.nb + p.I[0] / kBrick;
+        const int bx = p.I[0] / kBrick, by = p.I[1] / kBrick, bz = p.I[2] / kBrick;
+        key = (bz * a.nb + by) * a.nb + bx;
+        if (SCATTER) c = region_base<W>(p, bx * kBrick, by * kBrick, bz * kBrick) & 31;
     }
-    // warp aggregation: lanes with equal keys add once
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(peers) - 1;
@@ -119,11 +163,15 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
         uint32_t base = 0;
         if (valid && lane == leader) base = atomicAdd(&a.count[key], (uint32_t)__popc(peers));
         base = __shfl_sync(peers, base, leader);
-        if (valid) a.payload[base + rank] = (uint32_t)idx;
+        if (valid) {
+            a.payload[base + rank] = (uint32_t)idx;
+            a.cls[base + rank] = (uint8_t)c;
+        }
     }
 }
 
-// Single-block scan: cursor[b] = exclusive prefix of count; work items for each brick.
+// Single-block scan over bricks: cursor = exclusive prefix of count; work items
+// (brick, start, length) of at most kChunk points.
 __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__ count, uint32_t* __restrict__ cursor,
                                                     int nbricks, int4* __restrict__ work, int* __restrict__ counters,
                                                     int max_work) {
@@ -139,7 +187,6 @@ __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__
         pts += c;
         items += (int)((c + kChunk - 1) / kChunk);
     }
-    // block exclusive scan of (pts, items)
     const int lane = tid & 31, wid = tid >> 5;
     unsigned long long ip = pts;
     int ii = items;
@@ -181,6 +228,58 @@ __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__
     }
 }
 
+// Counting sort of each piece by bank class, in place; class_off[item * 32 + c] is the
+// offset of class c inside the piece.
+__global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ payload, const uint8_t* __restrict__ cls,
+                                                    const int4* __restrict__ work, const int* __restrict__ counters,
+                                                    uint32_t* __restrict__ class_off) {
+    __shared__ uint32_t s_ids[kChunk];
+    __shared__ uint8_t s_cls[kChunk];
+    __shared__ int s_hist[32], s_cur[32];
+    const int n_work = counters[0];
+    for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
+        const int4 wk = work[item];
+        if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < wk.z; i += blockDim.x) {
+            const uint32_t id = payload[wk.y + i];
+            const uint8_t c = cls[wk.y + i];
+            s_ids[i] = id;
+            s_cls[i] = c;
+            atomicAdd(&s_hist[c], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int h = s_hist[threadIdx.x];
+            int v = h;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if ((int)threadIdx.x >= o) v += u;
+            }
+            s_cur[threadIdx.x] = v - h;
+            class_off[(size_t)item * 32 + threadIdx.x] = (uint32_t)(v - h);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < wk.z; i += blockDim.x) {
+            const int slot = atomicAdd(&s_cur[s_cls[i]], 1);
+            payload[wk.y + slot] = s_ids[i];
+        }
+        __syncthreads();
+    }
+}
+
+template <int W>
+static void bin_w(Plan& P, const BinArgs& a0, long long blocks, int nbricks) {
+    Workspace& w = P.ws;
+    BinArgs a = a0;
+    k_bin<W, false><<<(unsigned)blocks, 256, 0, P.stream>>>(a);
+    k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work);
+    a.count = w.cursor;
+    k_bin<W, true><<<(unsigned)blocks, 256, 0, P.stream>>>(a);
+    k_class_sort<<<P.num_sms * 4, 256, 0, P.stream>>>(w.payload, w.cls, w.work, w.counters, w.class_off);
+}
+
 cudaError_t launch_bin(Plan& P, int M, bool kc) {
     Workspace& w = P.ws;
     const int G = kc ? P.Gk : P.Gr;
@@ -193,6 +292,7 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
     a.htab = w.htab;
     a.count = w.count;
     a.payload = w.payload;
+    a.cls = w.cls;
     a.npts = (long long)M * P.nH;
     a.nH = P.nH;
     a.G = G;
@@ -202,20 +302,31 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
     const long long blocks = (a.npts + 255) / 256;
     if (blocks == 0) {
         k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work);
+        P.launches += 1;
         return cudaGetLastError();
     }
-    k_bin<false><<<(unsigned)blocks, 256, 0, P.stream>>>(a);
-    k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work);
-    a.count = w.cursor;
-    k_bin<true><<<(unsigned)blocks, 256, 0, P.stream>>>(a);
+    switch (P.p.W) {
+        case 6: bin_w<6>(P, a, blocks, nbricks); break;
+        case 7: bin_w<7>(P, a, blocks, nbricks); break;
+        case 8: bin_w<8>(P, a, blocks, nbricks); break;
+        default: return cudaErrorInvalidValue;
+    }
+    P.launches += 4;
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Spreading
+//
+// Level 1: int32 fixed point in shared memory, one native shared-memory atomic add
+// per tap (v * S rounded to nearest through the FMA with 1.5 * 2^23).  S is a power
+// of two with max|w| * S <= 2^21, and level 1 is folded into the FP32 level-2 region
+// after every 512 points of the block (two per thread), so a cell can never exceed
+// 2^30.  Level 2 is added into the FP64 grid when the work item ends.
 // ---------------------------------------------------------------------------
 struct SpreadArgs {
     const uint32_t* payload;
+    const uint32_t* class_off;   // per work item: offset of each bank class in the piece
     const int4* work;
     int* counters;
     const ImgGeom* geom;
@@ -230,34 +341,35 @@ struct SpreadArgs {
 };
 
 constexpr int kSpreadThreads = 256;
+constexpr int kSpreadWarps = kSpreadThreads / 32;
 
-template <int W>
-__device__ __forceinline__ void window_taps(const KbPoly& P, float f, int& c, float* w) {
-    // first tap offset u in [0,1): taps at u + l - W/2, l = 0..W-1
-    constexpr float h = (W & 1) ? 0.5f : 0.0f;
-    const float t0 = f - h;
-    const float cf = ceilf(t0);
-    c = (int)cf;
-    const float z = 2.0f * (cf - t0) - 1.0f;
-#pragma unroll
-    for (int l = 0; l < W; ++l) {
-        float acc = P.c[l][kKbDeg];
-#pragma unroll
-        for (int j = kKbDeg - 1; j >= 0; --j) acc = fmaf(acc, z, P.c[l][j]);
-        w[l] = acc;
-    }
+__device__ __forceinline__ float2 point_weight(const SpreadArgs& a, bool cplx, int m, int t) {
+    if (cplx) return __ldg(&a.samples[(size_t)m * a.nH + t]);
+    const int g = min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1);
+    return make_float2(__ldg(&a.h2[(size_t)g * a.nH + t]), 0.0f);
 }
 
 template <int W, bool CPLX>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
     constexpr int RG = kBrick + W;
     constexpr int RG3 = RG * RG * RG;
-    extern __shared__ float sm[];           // CPLX: [re plane][im plane]
+    constexpr int NC = CPLX ? 2 : 1;
+    constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
+    constexpr int kMagicBits = 0x4B400000;
+    extern __shared__ int sm_i[];
+    int* lev1 = sm_i;                                  // NC * RG3 int32
+    float* lev2 = reinterpret_cast<float*>(sm_i + NC * RG3);   // NC * RG3 float
     __shared__ int s_item;
+    __shared__ float s_red[kSpreadWarps];
+    __shared__ int s_redi[kSpreadWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_work = a.counters[0];
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[1], 1);
-        for (int i = threadIdx.x; i < RG3 * (CPLX ? 2 : 1); i += blockDim.x) sm[i] = 0.0f;
+        for (int i = threadIdx.x; i < NC * RG3; i += blockDim.x) {
+            lev1[i] = 0;
+            lev2[i] = 0.0f;
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= n_work) break;
@@ -265,54 +377,83 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
         const int b = wk.x;
         const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
         const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * kBrick;
-        for (int j = threadIdx.x; j < wk.z; j += blockDim.x) {
-            const uint32_t id = __ldg(&a.payload[wk.y + j]);
+        // this lane's bank class inside the piece, this warp's share of it
+        const uint32_t s0 = (uint32_t)wk.y + __ldg(&a.class_off[(size_t)item * 32 + lane]);
+        const uint32_t s1 = (uint32_t)wk.y + (lane < 31 ? __ldg(&a.class_off[(size_t)item * 32 + lane + 1]) : (uint32_t)wk.z);
+        const int my_n = (int)(s1 - s0) > warp ? (int)((s1 - s0 - warp + kSpreadWarps - 1) / kSpreadWarps) : 0;
+        // scale from the largest weight of the item, rounds from the longest share
+        float wmax = 0.0f;
+        for (int i = 0; i < my_n; ++i) {
+            const uint32_t id = __ldg(&a.payload[s0 + warp + kSpreadWarps * i]);
             const int m = (int)(id / (uint32_t)a.nH);
-            const int t = (int)(id - (uint32_t)m * (uint32_t)a.nH);
-            const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
-            float wr, wi = 0.0f;
-            if (CPLX) {
-                const float2 s = __ldg(&a.samples[(size_t)m * a.nH + t]);
-                wr = s.x;
-                wi = s.y;
-            } else {
-                const int g = min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1);
-                wr = __ldg(&a.h2[(size_t)g * a.nH + t]);
-            }
-            float wx[W], wy[W], wz[W];
-            int cx, cy, cz;
-            window_taps<W>(a.poly, p.f[0], cx, wx);
-            window_taps<W>(a.poly, p.f[1], cy, wy);
-            window_taps<W>(a.poly, p.f[2], cz, wz);
-            const int r0 = p.I[0] - lo0 + cx, r1 = p.I[1] - lo1 + cy, r2 = p.I[2] - lo2 + cz;
-            if ((unsigned)r0 > (unsigned)kBrick || (unsigned)r1 > (unsigned)kBrick || (unsigned)r2 > (unsigned)kBrick) {
-                atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
-                continue;
-            }
-            const int base = (r2 * RG + r1) * RG + r0;
+            const float2 wv = point_weight(a, CPLX, m, (int)(id - (uint32_t)m * a.nH));
+            wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+        }
+        int rounds = (my_n + 1) / 2;
 #pragma unroll
-            for (int dz = 0; dz < W; ++dz) {
-                const float az = wr * wz[dz];
-                const float bzw = wi * wz[dz];
+        for (int o = 16; o > 0; o >>= 1) {
+            wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+            rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
+        }
+        if (lane == 0) { s_red[warp] = wmax; s_redi[warp] = rounds; }
+        __syncthreads();
+        wmax = s_red[0];
+        rounds = s_redi[0];
 #pragma unroll
-                for (int dy = 0; dy < W; ++dy) {
-                    const float ayz = az * wy[dy];
-                    const float byz = bzw * wy[dy];
-                    float* row = sm + base + (dz * RG + dy) * RG;
+        for (int i = 1; i < kSpreadWarps; ++i) { wmax = fmaxf(wmax, s_red[i]); rounds = max(rounds, s_redi[i]); }
+        int ex = 0;
+        if (wmax > 0.0f) frexpf(wmax, &ex);                // wmax <= 2^ex
+        const float S = ldexpf(1.0f, 21 - ex), invS = ldexpf(1.0f, ex - 21);
+        for (int r = 0; r < rounds; ++r) {
 #pragma unroll
-                    for (int dx = 0; dx < W; ++dx) {
-                        atomicAdd(row + dx, ayz * wx[dx]);
-                        if (CPLX) atomicAdd(row + RG3 + dx, byz * wx[dx]);
+            for (int q = 0; q < 2; ++q) {
+                const int i = 2 * r + q;
+                if (i >= my_n) continue;
+                const uint32_t id = __ldg(&a.payload[s0 + warp + kSpreadWarps * i]);
+                const int m = (int)(id / (uint32_t)a.nH);
+                const int t = (int)(id - (uint32_t)m * (uint32_t)a.nH);
+                const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
+                const int base = region_base<W>(p, lo0, lo1, lo2);
+                if (base < 0) {
+                    atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
+                    continue;
+                }
+                const float2 wv = point_weight(a, CPLX, m, t);
+                float wx[W], wy[W], wz[W];
+                window_taps<W>(a.poly, p.f[0], wx);
+                window_taps<W>(a.poly, p.f[1], wy);
+                window_taps<W>(a.poly, p.f[2], wz);
+                const float wr = wv.x * S, wi = wv.y * S;
+#pragma unroll
+                for (int dz = 0; dz < W; ++dz) {
+                    const float az = wr * wz[dz], bzw = wi * wz[dz];
+#pragma unroll
+                    for (int dy = 0; dy < W; ++dy) {
+                        const float ayz = az * wy[dy], byz = bzw * wy[dy];
+                        int* row = lev1 + base + (dz * RG + dy) * RG;
+#pragma unroll
+                        for (int dx = 0; dx < W; ++dx) {
+                            atomicAdd(row + dx, __float_as_int(fmaf(ayz, wx[dx], kMagic)) - kMagicBits);
+                            if (CPLX) atomicAdd(row + RG3 + dx, __float_as_int(fmaf(byz, wx[dx], kMagic)) - kMagicBits);
+                        }
                     }
                 }
             }
+            __syncthreads();
+            for (int i = threadIdx.x; i < NC * RG3; i += blockDim.x) {
+                const int v = lev1[i];
+                if (v != 0) {
+                    lev2[i] = fmaf((float)v, invS, lev2[i]);
+                    lev1[i] = 0;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        // flush the region into the FP64 grid (periodic wrap)
+        // add level 2 into the FP64 grid (periodic wrap)
         const int o0 = lo0 - W / 2, o1 = lo1 - W / 2, o2 = lo2 - W / 2;
         for (int i = threadIdx.x; i < RG3; i += blockDim.x) {
-            const float vr = sm[i];
-            const float vi = CPLX ? sm[RG3 + i] : 0.0f;
+            const float vr = lev2[i];
+            const float vi = CPLX ? lev2[RG3 + i] : 0.0f;
             if (vr == 0.0f && vi == 0.0f) continue;
             const int rx = i % RG, ry = (i / RG) % RG, rz = i / (RG * RG);
             int gx = o0 + rx, gy = o1 + ry, gz = o2 + rz;
@@ -337,7 +478,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
 template <int W, bool CPLX>
 static cudaError_t spread_w(Plan& P, const SpreadArgs& a) {
     constexpr int RG = kBrick + W;
-    const size_t smem = sizeof(float) * RG * RG * RG * (CPLX ? 2 : 1);
+    const size_t smem = sizeof(int) * RG * RG * RG * (CPLX ? 2 : 1) * 2;
     cudaError_t e = cudaFuncSetAttribute(k_spread<W, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -345,6 +486,7 @@ static cudaError_t spread_w(Plan& P, const SpreadArgs& a) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     k_spread<W, CPLX><<<P.num_sms * per_sm, kSpreadThreads, smem, P.stream>>>(a);
+    P.launches += 1;
     return cudaGetLastError();
 }
 
@@ -356,6 +498,7 @@ cudaError_t launch_spread(Plan& P, int M, bool kc) {
     if (e != cudaSuccess || M <= 0) return e;
     SpreadArgs a;
     a.payload = w.payload;
+    a.class_off = w.class_off;
     a.work = w.work;
     a.counters = w.counters;
     a.geom = w.geom;

@@ -54,6 +54,9 @@ class Reconstructor:
     def stage_times(self):
         return L.firm_stage_times(self.plan)
 
+    def launch_count(self) -> int:
+        return L.firm_launch_count(self.plan)
+
     # -- buffers ---------------------------------------------------------------------
     def half_shape(self):
         return (2 * self.N, 2 * self.N, self.N + 1)

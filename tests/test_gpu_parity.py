@@ -69,6 +69,7 @@ def test_kernel_and_khat_match_oracle(F, N, M, W, cfg):
     e_ker = rel(ker.cpu().numpy()[:, :, :N], _ker_half_from_oracle(Ker, N))
     e_kh = rel(khat.cpu().numpy(), O.khat_half(Ker.real))
     tol = 1e-5 if W >= 7 else 1.5e-5
+    print(f"Ker N={N} M={M} W={W}: rel err Ker {e_ker:.3e} K-hat {e_kh:.3e}")
     assert e_ker <= tol, e_ker
     assert e_kh <= tol, e_kh
     # lam_eff reads Ker(0); the closed form is sum h^2
@@ -107,7 +108,9 @@ def test_backprojection_matches_oracle(F, N, M, W, dtype):
     assert rel(s[..., 0] + 1j * s[..., 1], bH) <= 2e-6
     ref = O.backproject(img64, inp["shifts"], inp["R"], h, K)
     tol = 1e-5 if W >= 7 else 1.5e-5
-    assert rel(rhs.cpu().numpy(), ref) <= tol
+    e_rhs = rel(rhs.cpu().numpy(), ref)
+    print(f"A*b N={N} M={M} W={W} {dtype}: rel err {e_rhs:.3e}")
+    assert e_rhs <= tol
     rec.close()
 
 
