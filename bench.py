@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--images", type=int, default=None, help="override image count (smaller runs)")
     ap.add_argument("--N", type=int, default=None, help="override volume edge (profiling of smaller cases)")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER, help="CG iteration cap (profiling)")
-    ap.add_argument("--W", type=int, default=7)
+    ap.add_argument("--W", type=int, default=6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()

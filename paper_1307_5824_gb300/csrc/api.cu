@@ -214,8 +214,8 @@ static int check_params(const firm_params* p) {
     if (p->img_dtype != FIRM_IMG_F32 && p->img_dtype != FIRM_IMG_BF16) return FIRM_EINVAL;
     if (p->lambda_mode != FIRM_LAMBDA_RELATIVE && p->lambda_mode != FIRM_LAMBDA_ABSOLUTE) return FIRM_EINVAL;
     if (!(p->lambda >= 0.0)) return FIRM_EINVAL;
-    const double nH = (disc_size(p->N) + 1) / 2;
-    if ((double)p->M * nH >= 4294967295.0) return FIRM_EINVAL;   // point ids are 32-bit
+    // point ids are m << 13 | t: t < 8192 and m < 2^19
+    if ((disc_size(p->N) + 1) / 2 >= (1 << kTBits) || p->M >= (1 << (32 - kTBits))) return FIRM_EINVAL;
     return FIRM_OK;
 }
 
@@ -347,6 +347,7 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
     const int N = P.N, nH = P.nH;
     P.htab_host = half_disc(N);
     std::vector<float> h1((size_t)P.n_ctf * nH), h2((size_t)P.n_ctf * nH);
+    P.h2_max = 0.0f;
     for (int g = 0; g < P.n_ctf; ++g) {
         for (int t = 0; t < nH; ++t) {
             const int32_t kk = P.htab_host[t];
@@ -355,6 +356,7 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
             if (p->n_groups > 0) hv = ctf_value(P.groups[g], std::sqrt((double)(k1 * k1 + k2 * k2)) / (N * P.groups[g].pixel_A));
             h1[(size_t)g * nH + t] = (float)hv;
             h2[(size_t)g * nH + t] = (float)(hv * hv * (t == 0 ? 0.5 : 1.0));
+            P.h2_max = std::max(P.h2_max, h2[(size_t)g * nH + t]);
         }
     }
     auto tw = [](int L) {

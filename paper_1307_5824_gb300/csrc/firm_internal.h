@@ -12,9 +12,10 @@
 namespace firm {
 
 constexpr int kBrick = 8;             // spreading brick edge in fine-grid cells
-constexpr int kKbDeg = 9;             // degree of the per-tap window polynomials
+constexpr int kKbDeg = 7;             // degree of the per-tap window polynomials
 constexpr int kMaxW = 8;              // widest Kaiser-Bessel window supported
 constexpr int kChunk = 8192;          // most points one spreading work item takes
+constexpr int kTBits = 13;            // point id = m << kTBits | t (t < 8192)
 constexpr int kMaxHist = 20001;       // residual history capacity (iterations + 1)
 constexpr int kRedSlots = 4096;       // per-block partial sums of a reduction
 
@@ -101,6 +102,7 @@ struct Plan {
     size_t max_work = 0;
     KbPoly poly{};
     double lam_eff = 0.0;
+    float h2_max = 1.0f;           // largest kernel-channel weight (bounds the fixed-point scale)
     bool have_kernel = false, have_rhs = false;
     bool timing = false;
     // stage timing: events recorded around each stage when timing is on; read lazily

@@ -141,31 +141,39 @@ struct BinArgs {
 };
 
 template <int W, bool SCATTER>
-__global__ void __launch_bounds__(256) k_bin(BinArgs a) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = idx < a.npts;
-    int key = -1, c = 0;
-    if (valid) {
-        const int m = (int)(idx / a.nH);
-        const int t = (int)(idx - (long long)m * a.nH);
-        const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
-        const int bx = p.I[0] / kBrick, by = p.I[1] / kBrick, bz = p.I[2] / kBrick;
-        key = (bz * a.nb + by) * a.nb + bx;
-        if (SCATTER) c = region_base<W>(p, bx * kBrick, by * kBrick, bz * kBrick) & 31;
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
+__global__ void __launch_bounds__(256) k_bin(BinArgs a, int M) {
+    // x: samples t of one image (consecutive lanes walk a column of the half disc);
+    // y: images.  Runs of equal bricks among consecutive lanes are aggregated.
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (!SCATTER) {
-        if (valid && lane == leader) atomicAdd(&a.count[key], (uint32_t)__popc(peers));
-    } else {
-        uint32_t base = 0;
-        if (valid && lane == leader) base = atomicAdd(&a.count[key], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
+    for (int m = blockIdx.y; m < M; m += gridDim.y) {
+        const bool valid = t < a.nH;
+        int key = -1, c = 0;
         if (valid) {
-            a.payload[base + rank] = (uint32_t)idx;
-            a.cls[base + rank] = (uint8_t)c;
+            const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
+            const int bx = p.I[0] / kBrick, by = p.I[1] / kBrick, bz = p.I[2] / kBrick;
+            key = (bz * a.nb + by) * a.nb + bx;
+            if (SCATTER) c = region_base<W>(p, bx * kBrick, by * kBrick, bz * kBrick) & 31;
+        }
+        const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool head = (lane == 0) || (prev != key);
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        // run of this lane: from its head to the lane before the next head
+        const int my_head = 31 - __clz(heads & ((2u << lane) - 1u));
+        const unsigned later = heads & ~((2u << lane) - 1u);
+        const int next_head = later ? __ffs(later) - 1 : 32;
+        uint32_t base = 0;
+        if (valid && head) {
+            const int run = next_head - lane;
+            base = atomicAdd(&a.count[key], (uint32_t)run);
+        }
+        if (SCATTER) {
+            base = __shfl_sync(0xffffffffu, base, my_head);
+            if (valid) {
+                const uint32_t slot = base + (uint32_t)(lane - my_head);
+                a.payload[slot] = ((uint32_t)m << kTBits) | (uint32_t)t;
+                a.cls[slot] = (uint8_t)c;
+            }
         }
     }
 }
@@ -178,14 +186,15 @@ __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__
     __shared__ unsigned long long s_pts[32];
     __shared__ int s_items[32];
     const int T = blockDim.x, tid = threadIdx.x;
-    const int per = (nbricks + T - 1) / T;
+    const int per = ((nbricks + T - 1) / T + 3) & ~3;
     const int b0 = min(nbricks, tid * per), b1 = min(nbricks, b0 + per);
     unsigned long long pts = 0;
     int items = 0;
-    for (int b = b0; b < b1; ++b) {
-        const uint32_t c = count[b];
-        pts += c;
-        items += (int)((c + kChunk - 1) / kChunk);
+    for (int b = b0; b < b1; b += 4) {   // nbricks and per are multiples of 4
+        const uint4 c4 = *reinterpret_cast<const uint4*>(count + b);
+        pts += (unsigned long long)c4.x + c4.y + c4.z + c4.w;
+        items += (int)((c4.x + kChunk - 1) / kChunk) + (int)((c4.y + kChunk - 1) / kChunk) +
+                 (int)((c4.z + kChunk - 1) / kChunk) + (int)((c4.w + kChunk - 1) / kChunk);
     }
     const int lane = tid & 31, wid = tid >> 5;
     unsigned long long ip = pts;
@@ -270,14 +279,16 @@ __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ paylo
 }
 
 template <int W>
-static void bin_w(Plan& P, const BinArgs& a0, long long blocks, int nbricks) {
+static void bin_w(Plan& P, const BinArgs& a0, int nbricks) {
     Workspace& w = P.ws;
     BinArgs a = a0;
-    k_bin<W, false><<<(unsigned)blocks, 256, 0, P.stream>>>(a);
+    const int M = (int)(a.npts / a.nH);
+    const dim3 grid((a.nH + 255) / 256, (unsigned)(M < 65535 ? M : 65535));
+    k_bin<W, false><<<grid, 256, 0, P.stream>>>(a, M);
     k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work);
     a.count = w.cursor;
-    k_bin<W, true><<<(unsigned)blocks, 256, 0, P.stream>>>(a);
-    k_class_sort<<<P.num_sms * 4, 256, 0, P.stream>>>(w.payload, w.cls, w.work, w.counters, w.class_off);
+    k_bin<W, true><<<grid, 256, 0, P.stream>>>(a, M);
+    k_class_sort<<<P.num_sms * 5, 256, 0, P.stream>>>(w.payload, w.cls, w.work, w.counters, w.class_off);
 }
 
 cudaError_t launch_bin(Plan& P, int M, bool kc) {
@@ -306,9 +317,9 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
         return cudaGetLastError();
     }
     switch (P.p.W) {
-        case 6: bin_w<6>(P, a, blocks, nbricks); break;
-        case 7: bin_w<7>(P, a, blocks, nbricks); break;
-        case 8: bin_w<8>(P, a, blocks, nbricks); break;
+        case 6: bin_w<6>(P, a, nbricks); break;
+        case 7: bin_w<7>(P, a, nbricks); break;
+        case 8: bin_w<8>(P, a, nbricks); break;
         default: return cudaErrorInvalidValue;
     }
     P.launches += 4;
@@ -337,6 +348,7 @@ struct SpreadArgs {
     double* grid;             // G^3 real, or G^3 complex interleaved (re, im)
     int G, halfG, nb, nH, n_ctf;
     float scale;
+    float wmax_fixed;         // > 0: bound on |w| known in advance (no pre-pass)
     KbPoly poly;
 };
 
@@ -382,12 +394,13 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
         const uint32_t s1 = (uint32_t)wk.y + (lane < 31 ? __ldg(&a.class_off[(size_t)item * 32 + lane + 1]) : (uint32_t)wk.z);
         const int my_n = (int)(s1 - s0) > warp ? (int)((s1 - s0 - warp + kSpreadWarps - 1) / kSpreadWarps) : 0;
         // scale from the largest weight of the item, rounds from the longest share
-        float wmax = 0.0f;
-        for (int i = 0; i < my_n; ++i) {
-            const uint32_t id = __ldg(&a.payload[s0 + warp + kSpreadWarps * i]);
-            const int m = (int)(id / (uint32_t)a.nH);
-            const float2 wv = point_weight(a, CPLX, m, (int)(id - (uint32_t)m * a.nH));
-            wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+        float wmax = a.wmax_fixed;
+        if (wmax <= 0.0f) {
+            for (int i = 0; i < my_n; ++i) {
+                const uint32_t id = __ldg(&a.payload[s0 + warp + kSpreadWarps * i]);
+                const float2 wv = point_weight(a, CPLX, (int)(id >> kTBits), (int)(id & ((1u << kTBits) - 1u)));
+                wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+            }
         }
         int rounds = (my_n + 1) / 2;
 #pragma unroll
@@ -410,8 +423,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
                 const int i = 2 * r + q;
                 if (i >= my_n) continue;
                 const uint32_t id = __ldg(&a.payload[s0 + warp + kSpreadWarps * i]);
-                const int m = (int)(id / (uint32_t)a.nH);
-                const int t = (int)(id - (uint32_t)m * (uint32_t)a.nH);
+                const int m = (int)(id >> kTBits);
+                const int t = (int)(id & ((1u << kTBits) - 1u));
                 const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
                 const int base = region_base<W>(p, lo0, lo1, lo2);
                 if (base < 0) {
@@ -513,6 +526,7 @@ cudaError_t launch_spread(Plan& P, int M, bool kc) {
     a.nH = P.nH;
     a.n_ctf = P.n_ctf;
     a.scale = (float)(G / P.N);
+    a.wmax_fixed = kc ? P.h2_max : 0.0f;
     a.poly = P.poly;
     switch (P.p.W) {
         case 6: return kc ? spread_w<6, false>(P, a) : spread_w<6, true>(P, a);

@@ -11,7 +11,7 @@ class Reconstructor:
     """Owns one firm_plan: workspace from torch's caching allocator, stream = torch's
     current stream on `device`.  Methods forward to the C ABI of the same name."""
 
-    def __init__(self, N: int, M: int, groups=None, W: int = 7, lam: float = 0.0,
+    def __init__(self, N: int, M: int, groups=None, W: int = 6, lam: float = 0.0,
                  lambda_mode: int = L.FIRM_LAMBDA_RELATIVE, img_dtype: int = L.FIRM_IMG_F32,
                  device="cuda:0", stream=None):
         if not torch.cuda.is_available():
