@@ -132,6 +132,26 @@ int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, do
  * the last firm_kernel.  x and y are N^3 and must not overlap. */
 int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y);
 
+/* The same operator as firm_toeplitz_apply, y = Ker * x + lam_eff x, for callers that
+ * cannot allocate device memory and have no plan workspace to lend (for example a host
+ * application whose own allocator holds all device memory, or a code path that must not
+ * change the device memory footprint).  The paper has no counterpart: this is an
+ * interface variant.  It allocates nothing: the FFT scratch lives in one static device
+ * array inside the library, sized for N <= 64 (about 6.4 MB, resident on every device
+ * that loads the library until the process exits).
+ *   N       16, 32, 48 or 64; larger N is rejected with FIRM_EINVAL.
+ *   khat    K-hat half spectrum, 2N x 2N x (N+1) float32, device memory
+ *           (from firm_kernel(..., khat_out) or firm_copy_out(FIRM_OUT_KHAT)).
+ *   lam_eff Tikhonov weight added (>= 0), e.g. firm_lambda_eff of that plan.
+ *   x, y    N^3 float32 device arrays, distinct.
+ *   stream  cudaStream_t the passes are queued on; the call does not wait.
+ * The first call on a device looks up the array's device address (once per device,
+ * under a lock); make that first call before any stream capture.  All calls share the
+ * one array: calls whose work overlaps on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  Every pass writes its scratch before reading
+ * it, so nothing has to start at zero. */
+int firm_toeplitz_apply_static(int N, const float* khat, double lam_eff, const float* x, float* y, void* stream);
+
 /* lam_eff of the last firm_kernel (Tikhonov weight actually added to A*A). */
 int firm_lambda_eff(firm_plan_t plan, double* out);
 

@@ -21,7 +21,7 @@ FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES = 0, 1, 2, 3
 
 EXPORTED = [
     "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_cg_solve",
-    "firm_toeplitz_apply", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
+    "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
     "firm_stage_times", "firm_launch_count", "firm_destroy", "firm_strerror",
 ]
 
@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
     L.firm_backproject.argtypes = [vp, i, vp, vp, vp, vp, vp]
     L.firm_cg_solve.argtypes = [vp, vp, vp, i, d, vp, ctypes.POINTER(i)]
     L.firm_toeplitz_apply.argtypes = [vp, vp, vp]
+    L.firm_toeplitz_apply_static.argtypes = [i, vp, d, vp, vp, vp]
     L.firm_lambda_eff.argtypes = [vp, ctypes.POINTER(d)]
     L.firm_copy_out.argtypes = [vp, i, vp]
     L.firm_set_timing.argtypes = [vp, i]
@@ -155,6 +156,12 @@ def firm_cg_solve(plan, rhs, x, max_iter: int, rel_tol: float = 0.0, resid_hist=
 
 def firm_toeplitz_apply(plan, x, y):
     _check(lib().firm_toeplitz_apply(plan, _ptr(x), _ptr(y)), "firm_toeplitz_apply")
+
+
+def firm_toeplitz_apply_static(N: int, khat, lam_eff: float, x, y, stream: int = 0):
+    """y = Ker * x + lam_eff x without any device allocation (N <= 64; device arrays)."""
+    _check(lib().firm_toeplitz_apply_static(int(N), _ptr(khat), float(lam_eff), _ptr(x), _ptr(y), stream),
+           "firm_toeplitz_apply_static")
 
 
 def firm_lambda_eff(plan) -> float:

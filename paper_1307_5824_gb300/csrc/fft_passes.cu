@@ -17,6 +17,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <mutex>
+
 #include "fft.cuh"
 #include "firm_internal.h"
 
@@ -538,4 +541,107 @@ cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const 
     return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------
+// Toeplitz apply without any device allocation.
+//
+// For callers that cannot call cudaMalloc and have no workspace to lend: for
+// example a host application whose allocator already owns all device memory, or a
+// real-time path that must not change the device memory footprint while it runs.
+// The scratch of the five Toeplitz passes (and the FFT twiddle table) lives in
+// the file-scope array below instead; the caller still passes K-hat, x and y.
+// ---------------------------------------------------------------------------
+constexpr int kStaticMaxN = 64;
+constexpr size_t kStaticT1 = (size_t)kStaticMaxN * kStaticMaxN * (kStaticMaxN + 1);       // N x N x (N+1)
+constexpr size_t kStaticT2 = (size_t)kStaticMaxN * 2 * kStaticMaxN * (kStaticMaxN + 1);   // N x 2N x (N+1)
+constexpr size_t kStaticTw = 2 * kStaticMaxN;                                             // 2N twiddles
+static __device__ __align__(256) float2 g_static_scratch[kStaticT1 + kStaticT2 + kStaticTw];
+
+// Device address of g_static_scratch for the current device, looked up once per
+// device (host code cannot use the symbol itself as a device pointer).
+static int static_scratch(float2** out) {
+    static std::mutex mu;
+    static void* addr[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FIRM_ECUDA;
+    if (dev < 0 || dev >= 256) return FIRM_EINVAL;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return FIRM_ECUDA;
+        addr[dev] = p;
+    }
+    *out = reinterpret_cast<float2*>(addr[dev]);
+    return FIRM_OK;
+}
+
+template <int L>
+static cudaError_t toeplitz_static_l(float2* scratch, const float* khat, const float* x, float* y, float lam, int N,
+                                     cudaStream_t s) {
+    float2* t1 = scratch;
+    float2* t2 = scratch + kStaticT1;
+    float2* tw = scratch + kStaticT1 + kStaticT2;
+    float2 tw_h[L];                       // on the stack: no heap either
+    for (int j = 0; j < L; ++j) {
+        const double a = -2.0 * 3.14159265358979323846 * j / L;
+        tw_h[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    cudaError_t e = cudaMemcpyAsync(tw, tw_h, sizeof(tw_h), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    constexpr int ROWS = rows_per_block<L>();
+    const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
+    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
+    TRowsFwdOp a{{}, x, nullptr, nullptr, nullptr, t1, tw, N * N, N};
+    if ((e = cudaFuncSetAttribute(k_rows_cg<L, TRowsFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+        return e;
+    k_rows_cg<L, TRowsFwdOp><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, s>>>(a, nullptr);
+    TColsYFwdOp b{t1, t2, tw, N, N + 1, N};
+    if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, TColsYFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+        return e;
+    const int tiles_b = (N + 1 + kTX - 1) / kTX;
+    k_cols_cg<L, -1, TColsYFwdOp><<<N * tiles_b, kThreads, smem_cols, s>>>(b, nullptr);
+    const int n_inner = 2 * N * (N + 1);
+    if ((e = cudaFuncSetAttribute(k_toep_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols))) return e;
+    k_toep_z<L><<<(n_inner + kTX - 1) / kTX, kThreads, smem_cols, s>>>(t2, khat, tw, n_inner, N, nullptr);
+    TColsYInvOp d{t2, t1, tw, N, N + 1, N};
+    if ((e = cudaFuncSetAttribute(k_cols_cg<L, +1, TColsYInvOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+        return e;
+    k_cols_cg<L, +1, TColsYInvOp><<<N * tiles_b, kThreads, smem_cols, s>>>(d, nullptr);
+    const float scale = 1.0f / ((float)L * (float)L * (float)L);
+    TRowsInvOp f{t1, x, y, nullptr, nullptr, tw, N * N, N, scale, lam, nullptr};
+    if ((e = cudaFuncSetAttribute(k_toep_rows_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+        return e;
+    k_toep_rows_inv<L><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, s>>>(f);
+    return cudaGetLastError();
+}
+
 }  // namespace firm
+
+static bool on_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" int firm_toeplitz_apply_static(int N, const float* khat, double lam_eff, const float* x, float* y,
+                                          void* stream) {
+    using namespace firm;
+    if (N != 16 && N != 32 && N != 48 && N != 64) return FIRM_EINVAL;   // 64 is the static maximum
+    if (!khat || !x || !y || x == y || !(lam_eff >= 0.0)) return FIRM_EINVAL;
+    if (!on_device(khat) || !on_device(x) || !on_device(y)) return FIRM_EINVAL;
+    float2* scratch = nullptr;
+    const int st = static_scratch(&scratch);
+    if (st != FIRM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (2 * N) {
+        case 32: e = toeplitz_static_l<32>(scratch, khat, x, y, (float)lam_eff, N, s); break;
+        case 64: e = toeplitz_static_l<64>(scratch, khat, x, y, (float)lam_eff, N, s); break;
+        case 96: e = toeplitz_static_l<96>(scratch, khat, x, y, (float)lam_eff, N, s); break;
+        case 128: e = toeplitz_static_l<128>(scratch, khat, x, y, (float)lam_eff, N, s); break;
+        default: break;
+    }
+    return e == cudaSuccess ? FIRM_OK : FIRM_ECUDA;
+}
