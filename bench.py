@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--N", type=int, default=None, help="override volume edge (profiling of smaller cases)")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER, help="CG iteration cap (profiling)")
     ap.add_argument("--W", type=int, default=6)
+    ap.add_argument("--precond", default="none", choices=["none", "circulant", "binned", "learned"])
+    ap.add_argument("--train-kernels", type=int, default=2000, help="N=64 kernels the learned preconditioner trains on")
+    ap.add_argument("--workload", default="C3", choices=["C3", "C5"],
+                    help="C3: 50k Haar views, 20 groups; C5: 40k views 85%% in a 15 degree cap, 8 groups")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -106,9 +110,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def workload(M_override=None, N_override=None):
+def workload(M_override=None, N_override=None, name=WORKLOAD):
     import synth
-    inp = synth.config_inputs(WORKLOAD, M=M_override, N=N_override)
+    inp = synth.config_inputs(name, M=M_override, N=N_override)
     return inp
 
 
@@ -210,7 +214,7 @@ def main():
     torch.cuda.set_device(dev)
 
     t_syn = time.perf_counter()
-    inp = workload(args.images, args.N)
+    inp = workload(args.images, args.N, args.workload)
     t_syn = time.perf_counter() - t_syn
     N, M = inp["N"], inp["M"]
     nK = disc_size(N)
@@ -226,11 +230,27 @@ def main():
     inp["images"] = inp["images"][:5000].copy()     # the CPU-baseline sample keeps a few
 
     rec = Reconstructor(N, M, groups=inp["groups"], W=args.W, lam=1e-3, img_dtype=L.FIRM_IMG_BF16, device=dev)
+    pc_modes = {"none": L.FIRM_PRECOND_NONE, "circulant": L.FIRM_PRECOND_CIRCULANT,
+                "binned": L.FIRM_PRECOND_BINNED, "learned": L.FIRM_PRECOND_TABLE}
+    net = None
+    train_info = None
+    if args.precond == "learned":
+        from paper_1307_5824_gb300 import learned
+        t0 = time.perf_counter()
+        X, T = learned.generate(args.train_kernels, N=64, device=dev)
+        t_gen = time.perf_counter() - t0
+        net, hist = learned.train(X[: int(0.9 * len(X))], T[: int(0.9 * len(X))], device=dev)
+        train_info = {"kernels": int(len(X)), "gen_s": round(t_gen, 1), "loss": hist,
+                      "val_mse_bf16": learned.evaluate(net, X[int(0.9 * len(X)):], T[int(0.9 * len(X)):], bf16=True)}
+    else:
+        rec.set_precond(pc_modes[args.precond])
     x = torch.empty((N, N, N), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(R_, g_, s_, im_, x_):
         rec.kernel(R_, g_)
+        if net is not None:
+            learned.apply_learned(rec, net)
         rec.backproject(im_, s_, R_, g_)
         st, it = rec.cg_solve(x_, args.max_iter, rel_tol=REL_TOL, allow=(L.FIRM_ENOTCONV,))
         return st, it
@@ -342,6 +362,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "synth_s": round(t_syn, 1),
+        "precond": args.precond,
+        "learned_training": train_info,
     }
     print(json.dumps(out))
     if world > 1:

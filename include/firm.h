@@ -127,6 +127,62 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
 int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, double rel_tol,
                   double* resid_hist, int* iters_out);
 
+/* Preconditioner used by firm_cg_solve from its next call on (north star; the paper's
+ * CG is unpreconditioned).  FIRM_PRECOND_NONE: plain CG (Section 3.3).
+ * FIRM_PRECOND_CIRCULANT: z = F^-1 diag(1 / (kappa(k) + lam_eff)) F r on the N^3 grid,
+ * kappa the spectrum of T. Chan's optimal circulant of the Toeplitz operator (the
+ * circulant nearest to it in Frobenius norm; column sum over n = m mod N of
+ * Ker(n) prod_a (N - |n_a|)/N), built on the circulant diagonalisation of Section 2.3.
+ * kappa >= 0 for A*A; the floor is lam_eff (or 1e-6 kappa(0) when lam_eff = 0).  The
+ * stopping test stays ||r_k|| <= rel_tol ||rhs||; beta is the flexible (Polak-Ribiere)
+ * form, equal to the textbook one in exact arithmetic.
+ * FIRM_PRECOND_BINNED: the same Fourier diagonal averaged per radial-angular bin (64 shells
+ * of |q|/(N/2) x 16 cones of |cos| to the principal viewing axis; see firm_pc_target) --
+ * the direct, network-free control of the learned preconditioner.
+ * FIRM_PRECOND_TABLE: the per-bin table given to firm_set_precond_table (for example the
+ * learned network's output). */
+enum { FIRM_PRECOND_NONE = 0, FIRM_PRECOND_CIRCULANT = 1, FIRM_PRECOND_BINNED = 2, FIRM_PRECOND_TABLE = 3 };
+int firm_set_precond(firm_plan_t plan, int mode);
+
+/* Learned-preconditioner interface (north star; no counterpart in the paper).  Bins: a
+ * frequency q (N-grid units) is in shell s = min(63, floor(64 |q| / (N/2))) and cone
+ * c = min(15, floor(16 |<q/|q|, a>|)), bin = 16 s + c, a = firm_pc_axis (eigenvector of
+ * the largest eigenvalue of the second moment of the viewing directions R_m^T e3 of
+ * the last firm_kernel).
+ * firm_pc_features: h^2-weighted density of the slice samples per bin, summing to 1
+ *   (1024 floats, host or device).
+ * firm_pc_target: t_b = log(p_b Ker(0)), p_b = sum (kappa + lam_eff) / sum (kappa +
+ *   lam_eff)^2 over the bin, kappa the spectrum of FIRM_PRECOND_CIRCULANT (least-squares
+ *   fit of 1/(kappa + lam_eff) by one value per bin); empty bins copy the nearest
+ *   non-empty shell of the same cone.
+ * firm_set_precond_table: use d(q) = exp(table_log[bin(q)]) / Ker(0) as the
+ *   preconditioner (selects FIRM_PRECOND_TABLE). */
+int firm_pc_features(firm_plan_t plan, float* out1024);
+int firm_pc_target(firm_plan_t plan, float* out1024);
+int firm_pc_axis(firm_plan_t plan, float* out3);
+int firm_set_precond_table(firm_plan_t plan, const float* table_log1024);
+
+/* The network of the learned preconditioner: 1024 -> 256 -> 256 -> 1024 with ReLU, input
+ * x_b = log(1024 f_b + 1e-3) of the features, output the log table t.  Parameters are one
+ * float32 array of firm_mlp_param_count() values: W1 (256 x 1024), b1, W2 (256 x 256),
+ * b2, W3 (1024 x 256), b3 (W row-major, out x in).  All arrays are device memory; work
+ * holds firm_mlp_work_floats(batch) floats; calls are queued on `stream`.
+ *   forward:   y (batch x 1024) from x (batch x 1024), FP32.
+ *   to_bf16 / forward_bf16: BF16 copy of the weights (2 bytes each) and the forward pass
+ *              with BF16 weights, FP32 biases and FP32 accumulation (inference).
+ *   grad:      mean squared error of y against t and its gradient (same layout as the
+ *              parameters); *loss is device memory.
+ *   adam:      one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step counted from 1). */
+int firm_mlp_param_count(void);
+size_t firm_mlp_work_floats(int batch);
+int firm_mlp_forward(const float* params, int batch, const float* x, float* y, float* work, void* stream);
+int firm_mlp_to_bf16(const float* params, void* params_bf16, void* stream);
+int firm_mlp_forward_bf16(const void* params_bf16, const float* params, int batch, const float* x, float* y,
+                          float* work, void* stream);
+int firm_mlp_grad(const float* params, int batch, const float* x, const float* t, float* grad, float* work,
+                  double* loss, void* stream);
+int firm_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, void* stream);
+
 /* One application of the regularised normal operator, y = Ker * x + lam_eff x
  * (eq. property through the circulant embedding of Section 3.2), using the K-hat of
  * the last firm_kernel.  x and y are N^3 and must not overlap. */

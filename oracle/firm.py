@@ -35,7 +35,8 @@ __all__ = [
     "disc", "electron_wavelength_A", "ctf", "ctf_weights", "slice_points",
     "forward", "adjoint", "kernel", "kernel_at", "adjoint_at", "image_dft",
     "backproject", "backproject_at", "circulant_column", "khat", "khat_half",
-    "toeplitz_direct", "toeplitz_apply", "lambda_eff", "cg",
+    "toeplitz_direct", "toeplitz_apply", "lambda_eff", "cg", "wrapped_spectrum",
+    "circulant_preconditioner",
 ]
 
 
@@ -334,3 +335,39 @@ def cg(apply, rhs: np.ndarray, max_iter: int, rel_tol: float = 0.0, x0=None, pre
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, np.array(hist), it
+
+
+# ----------------------------------------------------------------------------
+# Circulant preconditioner (north star; built on the circulant diagonalisation of
+# Section 2.3, eq. circ1)
+# ----------------------------------------------------------------------------
+
+def wrapped_spectrum(Ker: np.ndarray, weighted: bool = True) -> np.ndarray:
+    """Eigenvalues of an N-periodic circulant built from the Toeplitz kernel (Section 2.3).
+
+    weighted=True: T. Chan's optimal circulant (the circulant nearest to the Toeplitz
+    matrix in Frobenius norm): c(m) = sum over n = m (mod N), n in (-N, N)^3, of
+    Ker(n) prod_a (N - |n_a|) / N.  weighted=False: the plain wrap, whose spectrum is
+    K-hat at even frequencies.  The lag -N planes are excluded (reading 2).
+    Returns the real N^3 spectrum (FFT_N of c)."""
+    N = Ker.shape[0] // 2
+    K = Ker.real.copy()
+    K[0], K[:, 0], K[:, :, 0] = 0.0, 0.0, 0.0          # lag -N planes
+    if weighted:
+        w = (N - np.abs(np.arange(-N, N))) / N
+        K = K * w[:, None, None] * w[None, :, None] * w[None, None, :]
+    c = np.zeros((N, N, N))
+    # storage block a covers n in [-N + aN, aN); its index i is n + N - aN == n (mod N)
+    for a in range(2):
+        for b in range(2):
+            for d in range(2):
+                c += K[a * N:(a + 1) * N, b * N:(b + 1) * N, d * N:(d + 1) * N]
+    return np.fft.fftn(c).real
+
+
+def circulant_preconditioner(kappa: np.ndarray, lam_eff: float):
+    """z = F^-1 diag(1 / (max(kappa, 0) + floor)) F r, floor = lam_eff (or 1e-6 kappa(0)
+    when lam_eff = 0): the inverse of the circulant approximation of (A*A + lam_eff I)."""
+    floor = lam_eff if lam_eff > 0 else 1e-6 * float(kappa[0, 0, 0])
+    d = 1.0 / (np.maximum(kappa, 0.0) + floor)
+    return lambda r: np.fft.ifftn(d * np.fft.fftn(r)).real

@@ -18,11 +18,14 @@ FIRM_OK, FIRM_EINVAL, FIRM_ENOMEM, FIRM_ECUDA, FIRM_ENOTCONV, FIRM_EBREAKDOWN, F
 FIRM_IMG_F32, FIRM_IMG_BF16 = 0, 1
 FIRM_LAMBDA_RELATIVE, FIRM_LAMBDA_ABSOLUTE = 0, 1
 FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES = 0, 1, 2, 3
+FIRM_PRECOND_NONE, FIRM_PRECOND_CIRCULANT, FIRM_PRECOND_BINNED, FIRM_PRECOND_TABLE = 0, 1, 2, 3
 
 EXPORTED = [
     "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_cg_solve",
-    "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
-    "firm_stage_times", "firm_launch_count", "firm_destroy", "firm_strerror",
+    "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_set_precond", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
+    "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_target", "firm_pc_axis",
+    "firm_set_precond_table", "firm_mlp_forward", "firm_mlp_to_bf16", "firm_mlp_forward_bf16", "firm_mlp_grad",
+    "firm_mlp_adam", "firm_mlp_param_count", "firm_mlp_work_floats", "firm_destroy", "firm_strerror",
 ]
 
 
@@ -64,17 +67,29 @@ def lib() -> ctypes.CDLL:
     L.firm_cg_solve.argtypes = [vp, vp, vp, i, d, vp, ctypes.POINTER(i)]
     L.firm_toeplitz_apply.argtypes = [vp, vp, vp]
     L.firm_toeplitz_apply_static.argtypes = [i, vp, d, vp, vp, vp]
+    L.firm_set_precond.argtypes = [vp, i]
     L.firm_lambda_eff.argtypes = [vp, ctypes.POINTER(d)]
     L.firm_copy_out.argtypes = [vp, i, vp]
     L.firm_set_timing.argtypes = [vp, i]
     L.firm_stage_times.argtypes = [vp, ctypes.POINTER(d), i]
     L.firm_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    for n in ("firm_pc_features", "firm_pc_target", "firm_pc_axis", "firm_set_precond_table"):
+        getattr(L, n).argtypes = [vp, vp]
+    L.firm_mlp_forward.argtypes = [vp, i, vp, vp, vp, vp]
+    L.firm_mlp_to_bf16.argtypes = [vp, vp, vp]
+    L.firm_mlp_forward_bf16.argtypes = [vp, vp, i, vp, vp, vp, vp]
+    L.firm_mlp_grad.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+    L.firm_mlp_adam.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, vp]
+    L.firm_mlp_param_count.argtypes = []
+    L.firm_mlp_work_floats.argtypes = [i]
+    L.firm_mlp_work_floats.restype = ctypes.c_size_t
     L.firm_destroy.argtypes = [vp]
     L.firm_destroy.restype = None
     L.firm_strerror.argtypes = [i]
     L.firm_strerror.restype = ctypes.c_char_p
     for name in EXPORTED[:-2]:
-        getattr(L, name).restype = ctypes.c_int
+        if name != "firm_mlp_work_floats":
+            getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
 
@@ -164,6 +179,10 @@ def firm_toeplitz_apply_static(N: int, khat, lam_eff: float, x, y, stream: int =
            "firm_toeplitz_apply_static")
 
 
+def firm_set_precond(plan, mode: int):
+    _check(lib().firm_set_precond(plan, int(mode)), "firm_set_precond")
+
+
 def firm_lambda_eff(plan) -> float:
     v = ctypes.c_double(0)
     _check(lib().firm_lambda_eff(plan, ctypes.byref(v)), "firm_lambda_eff")
@@ -192,6 +211,55 @@ def firm_launch_count(plan) -> int:
     v = ctypes.c_longlong(0)
     _check(lib().firm_launch_count(plan, ctypes.byref(v)), "firm_launch_count")
     return int(v.value)
+
+
+def firm_pc_features(plan, out):
+    _check(lib().firm_pc_features(plan, _ptr(out)), "firm_pc_features")
+
+
+def firm_pc_target(plan, out):
+    _check(lib().firm_pc_target(plan, _ptr(out)), "firm_pc_target")
+
+
+def firm_pc_axis(plan):
+    out = np.zeros(3, np.float32)
+    _check(lib().firm_pc_axis(plan, out.ctypes.data), "firm_pc_axis")
+    return out
+
+
+def firm_set_precond_table(plan, table_log):
+    _check(lib().firm_set_precond_table(plan, _ptr(table_log)), "firm_set_precond_table")
+
+
+def firm_mlp_param_count() -> int:
+    return int(lib().firm_mlp_param_count())
+
+
+def firm_mlp_work_floats(batch: int) -> int:
+    return int(lib().firm_mlp_work_floats(int(batch)))
+
+
+def firm_mlp_forward(params, batch, x, y, work, stream=0):
+    _check(lib().firm_mlp_forward(_ptr(params), int(batch), _ptr(x), _ptr(y), _ptr(work), stream), "firm_mlp_forward")
+
+
+def firm_mlp_to_bf16(params, params_bf16, stream=0):
+    _check(lib().firm_mlp_to_bf16(_ptr(params), _ptr(params_bf16), stream), "firm_mlp_to_bf16")
+
+
+def firm_mlp_forward_bf16(params_bf16, params, batch, x, y, work, stream=0):
+    _check(lib().firm_mlp_forward_bf16(_ptr(params_bf16), _ptr(params), int(batch), _ptr(x), _ptr(y), _ptr(work),
+                                       stream), "firm_mlp_forward_bf16")
+
+
+def firm_mlp_grad(params, batch, x, t, grad, work, loss, stream=0):
+    _check(lib().firm_mlp_grad(_ptr(params), int(batch), _ptr(x), _ptr(t), _ptr(grad), _ptr(work), _ptr(loss), stream),
+           "firm_mlp_grad")
+
+
+def firm_mlp_adam(params, grad, m, v, step, lr, stream=0):
+    _check(lib().firm_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), stream),
+           "firm_mlp_adam")
 
 
 def firm_destroy(plan):

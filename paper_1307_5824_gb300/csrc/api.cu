@@ -192,6 +192,12 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.q = c.take<float>(N3);
     w.t1 = c.take<float2>(N * N * (N + 1));
     w.t2 = c.take<float2>(N * 2 * N * (N + 1));
+    w.z = c.take<float>(N3);
+    w.pc_diag = c.take<float>(N * N * (N / 2 + 1) + 1);
+    w.pc_feat = c.take<float>(1024);
+    w.pc_table = c.take<float>(1024);
+    w.pc_s1 = c.take<double>(1024);
+    w.pc_s2 = c.take<double>(1024);
     w.red_a = c.take<double>(kRedSlots);
     w.red_b = c.take<double>(kRedSlots);
     w.hist = c.take<double>(kMaxHist);
@@ -282,6 +288,57 @@ static int check_spread_flag(Plan& P) {
     FIRM_CK(cudaMemcpyAsync(&flag, P.ws.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
     FIRM_CK(cudaStreamSynchronize(P.stream));
     return flag ? FIRM_ECUDA : FIRM_OK;
+}
+
+
+// Per-bin log target t_b = log(p_b Ker(0)), p_b = s1 / s2; empty bins take the value of
+// the nearest non-empty shell of the same cone (all empty: the mean of the others).
+static void finalize_target(const double* s1, const double* s2, double ker0, float* t) {
+    const int S = 64, C = 16;
+    std::vector<double> v(1024, NAN);
+    double sum = 0.0;
+    int cnt = 0;
+    for (int b = 0; b < 1024; ++b)
+        if (s2[b] > 0.0) { v[b] = std::log(s1[b] / s2[b] * ker0); sum += v[b]; ++cnt; }
+    const double mean = cnt ? sum / cnt : 0.0;
+    for (int c = 0; c < C; ++c)
+        for (int s = 0; s < S; ++s) {
+            if (!std::isnan(v[C * s + c])) { t[C * s + c] = (float)v[C * s + c]; continue; }
+            int best = -1;
+            for (int d = 1; d < S && best < 0; ++d) {
+                if (s - d >= 0 && !std::isnan(v[C * (s - d) + c])) best = s - d;
+                else if (s + d < S && !std::isnan(v[C * (s + d) + c])) best = s + d;
+            }
+            t[C * s + c] = (float)(best >= 0 ? v[C * best + c] : mean);
+        }
+}
+
+static int compute_target(Plan& P, float* t_host) {
+    FIRM_CK(launch_chan_spectrum(P));
+    FIRM_CK(launch_pc_target_sums(P, P.ws.pc_s1, P.ws.pc_s2));
+    std::vector<double> s1(1024), s2(1024);
+    FIRM_CK(cudaMemcpyAsync(s1.data(), P.ws.pc_s1, 1024 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaMemcpyAsync(s2.data(), P.ws.pc_s2, 1024 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    finalize_target(s1.data(), s2.data(), P.ker0, t_host);
+    return FIRM_OK;
+}
+
+static int build_preconditioner(Plan& P) {
+    if (P.pc_mode == FIRM_PRECOND_CIRCULANT) {
+        FIRM_CK(launch_chan_spectrum(P));
+        FIRM_CK(launch_pc_build_circulant(P));
+        return FIRM_OK;
+    }
+    if (P.pc_mode == FIRM_PRECOND_BINNED) {
+        std::vector<float> t(1024);
+        const int st = compute_target(P, t.data());
+        if (st != FIRM_OK) return st;
+        FIRM_CK(cudaMemcpyAsync(P.ws.pc_table, t.data(), 1024 * sizeof(float), cudaMemcpyHostToDevice, P.stream));
+    }
+    // FIRM_PRECOND_TABLE: pc_table was set by firm_set_precond_table
+    FIRM_CK(launch_pc_from_table(P, P.ws.pc_table));
+    return FIRM_OK;
 }
 
 }  // namespace firm
@@ -433,7 +490,11 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     int st = check_spread_flag(P);
     if (st != FIRM_OK) return st;
     P.lam_eff = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda * (double)ker0 : P.p.lambda;
+    P.ker0 = ker0 > 0.0f ? ker0 : 1.0f;
+    P.last_M = M;
+    if (M > 0) FIRM_CK(launch_view_axis(P, P.cur_R, M));
     P.have_kernel = true;
+    P.pc_ready = false;
     return put_out(khat_out, w.khat, sizeof(float) * 2 * P.N * 2 * P.N * (P.N + 1), P.stream);
 }
 
@@ -508,11 +569,19 @@ int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, do
     FIRM_CK(e);
     StageTimer tm(P);
     tm.start(8);
-    FIRM_CK(launch_cg_init(P, rd, max_iter, rel_tol));
+    const bool use_pc = P.pc_mode != FIRM_PRECOND_NONE;
+    if (use_pc && !P.pc_ready) {
+        int st = build_preconditioner(P);
+        if (st != FIRM_OK) return st;
+        P.pc_ready = true;
+    }
+    FIRM_CK(launch_cg_init(P, rd, max_iter, rel_tol, use_pc));
+    if (use_pc) FIRM_CK(launch_precond(P, w.r, w.z, w.cg));
     const int batch = 8;
     for (int it = 0; it < max_iter; ++it) {
-        FIRM_CK(launch_toeplitz(P, w.p, w.q, (float)P.lam_eff, w.r, w.cg));
+        FIRM_CK(launch_toeplitz(P, w.p, w.q, (float)P.lam_eff, w.r, w.cg, use_pc ? w.z : nullptr));
         FIRM_CK(launch_cg_update(P));
+        if (use_pc) FIRM_CK(launch_precond(P, w.r, w.z, w.cg));
         if (rel_tol > 0.0 && ((it + 1) % batch == 0) && it + 1 < max_iter) {
             int done = 0;
             FIRM_CK(cudaMemcpyAsync(&done, &w.cg->done, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
@@ -536,6 +605,62 @@ int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, do
     FIRM_CK(cudaStreamSynchronize(P.stream));
     if (s.status != FIRM_OK) return s.status;
     if (rel_tol > 0.0 && !(s.rr >= 0.0 && std::sqrt(s.rr) <= s.tol)) return FIRM_ENOTCONV;
+    return FIRM_OK;
+}
+
+int firm_set_precond(firm_plan_t plan, int mode) {
+    if (!plan) return FIRM_EINVAL;
+    if (mode != FIRM_PRECOND_NONE && mode != FIRM_PRECOND_CIRCULANT && mode != FIRM_PRECOND_BINNED &&
+        mode != FIRM_PRECOND_TABLE)
+        return FIRM_EINVAL;
+    plan->P.pc_mode = mode;
+    plan->P.pc_ready = false;
+    return FIRM_OK;
+}
+
+int firm_set_precond_table(firm_plan_t plan, const float* table_log) {
+    if (!plan || !table_log) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    cudaError_t e = cudaSuccess;
+    const float* d = stage(table_log, P.ws.pc_table, 1024, P.stream, e);
+    FIRM_CK(e);
+    if (d != P.ws.pc_table) FIRM_CK(cudaMemcpyAsync(P.ws.pc_table, d, 1024 * sizeof(float), cudaMemcpyDeviceToDevice, P.stream));
+    P.pc_mode = FIRM_PRECOND_TABLE;
+    P.pc_ready = false;
+    return FIRM_OK;
+}
+
+int firm_pc_features(firm_plan_t plan, float* out) {
+    if (!plan || !out) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!P.have_kernel) return FIRM_ESTATE;
+    FIRM_CK(launch_pc_features(P, P.last_M, P.ws.pc_feat));
+    std::vector<float> h(1024);
+    FIRM_CK(cudaMemcpyAsync(h.data(), P.ws.pc_feat, 1024 * sizeof(float), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    double tot = 0.0;
+    for (float v : h) tot += v;
+    for (float& v : h) v = tot > 0.0 ? (float)(v / tot) : 0.0f;
+    FIRM_CK(cudaMemcpyAsync(P.ws.pc_feat, h.data(), 1024 * sizeof(float), cudaMemcpyHostToDevice, P.stream));
+    return put_out(out, P.ws.pc_feat, 1024 * sizeof(float), P.stream);
+}
+
+int firm_pc_target(firm_plan_t plan, float* out) {
+    if (!plan || !out) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!P.have_kernel) return FIRM_ESTATE;
+    std::vector<float> t(1024);
+    const int st = compute_target(P, t.data());
+    if (st != FIRM_OK) return st;
+    P.pc_ready = false;                 // ws.t1 was used as scratch
+    FIRM_CK(cudaMemcpyAsync(P.ws.pc_s1, t.data(), 1024 * sizeof(float), cudaMemcpyHostToDevice, P.stream));
+    return put_out(out, P.ws.pc_s1, 1024 * sizeof(float), P.stream);
+}
+
+int firm_pc_axis(firm_plan_t plan, float* out3) {
+    if (!plan || !out3) return FIRM_EINVAL;
+    if (!plan->P.have_kernel) return FIRM_ESTATE;
+    for (int i = 0; i < 3; ++i) out3[i] = plan->P.pc_axis[i];
     return FIRM_OK;
 }
 

@@ -56,7 +56,7 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket, bool* s_last) {
 __global__ void __launch_bounds__(kCgThreads) k_cg_init(const float* __restrict__ rhs, float* __restrict__ x,
                                                         double* __restrict__ r, float* __restrict__ p, size_t n,
                                                         CgState* cg, double* red, double* hist, int max_iter,
-                                                        double rel_tol) {
+                                                        double rel_tol, int use_pc) {
     __shared__ double s_warp[kCgThreads / 32];
     __shared__ double s_fin[kCgThreads];
     __shared__ bool s_last;
@@ -81,6 +81,9 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(const float* __restrict_
         cg->it = 0;
         cg->max_iter = max_iter;
         cg->status = FIRM_OK;
+        cg->rz = 0.0;
+        cg->use_pc = use_pc;
+        cg->first = 1;
         cg->done = (rr == 0.0 || max_iter <= 0 || (cg->tol > 0.0 && sqrt(rr) <= cg->tol)) ? 1 : 0;
         if (!(rr == rr) || rr > 1.7e308) { cg->done = 1; cg->status = FIRM_EBREAKDOWN; }
         hist[0] = sqrt(rr);
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x,
     __shared__ bool s_last;
     if (cg->done) return;
     const double pq = cg->pq, rr = cg->rr;
-    const double alpha = rr / pq;
+    const double alpha = (cg->use_pc ? cg->rz : rr) / pq;
     const bool ok = pq > 0.0 && isfinite(alpha);
     double acc = 0.0;
     if (ok) {
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x,
             const int it = cg->it + 1;
             cg->it = it;
             hist[it < kMaxHist ? it : kMaxHist - 1] = sqrt(rr_new);
-            cg->beta = rr_new / rr;
+            if (!cg->use_pc) cg->beta = rr_new / rr;    // else set by the preconditioner pass
             cg->rr = rr_new;
             if (cg->tol > 0.0 && sqrt(rr_new) <= cg->tol) cg->done = 1;
             if (it >= cg->max_iter) cg->done = 1;
@@ -145,13 +148,13 @@ static int cg_blocks(const Plan& P) {
     return b < kRedSlots ? b : kRedSlots;
 }
 
-cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_tol) {
+cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_tol, bool use_pc) {
     Workspace& w = P.ws;
     const size_t n = (size_t)P.N * P.N * P.N;
     cudaError_t e = cudaMemsetAsync(w.cg, 0, sizeof(CgState), P.stream);
     if (e != cudaSuccess) return e;
     k_cg_init<<<cg_blocks(P), kCgThreads, 0, P.stream>>>(rhs, w.x, w.r, w.p, n, w.cg, w.red_b, w.hist, max_iter,
-                                                         rel_tol);
+                                                         rel_tol, use_pc ? 1 : 0);
     P.launches += 1;
     return cudaGetLastError();
 }

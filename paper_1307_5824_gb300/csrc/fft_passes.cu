@@ -354,11 +354,12 @@ cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* s
 // ---------------------------------------------------------------------------
 struct TRowsFwdOp : NoFinish {
     const float* x; float* p; const double* r; const CgState* cg; float2* out; const float2* tw; int n_rows, N;
+    const float* z = nullptr;   // preconditioned residual: p = z + beta p when set
     __device__ __forceinline__ float2 load(int row, int n) const {
         if (n >= N) return make_float2(0.0f, 0.0f);
         const size_t i = (size_t)row * N + n;
-        if (cg) {   // p = r + beta p (r FP64), written back
-            const float v = (float)fma(cg->beta, (double)p[i], __ldg(&r[i]));
+        if (cg) {   // p = r + beta p (r FP64) or p = z + beta p, written back
+            const float v = (float)fma(cg->beta, (double)p[i], z ? (double)__ldg(&z[i]) : __ldg(&r[i]));
             p[i] = v;
             return make_float2(v, 0.0f);
         }
@@ -499,7 +500,8 @@ __global__ void __launch_bounds__(kThreads) k_cols_cg(const Op op, const CgState
 }
 
 template <int L>
-static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg) {
+static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg,
+                              const float* cg_z) {
     Workspace& w = P.ws;
     const int N = P.N;
     constexpr int ROWS = rows_per_block<L>();
@@ -507,7 +509,7 @@ static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, cons
     const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
     cudaError_t e;
     // pass 1: rows of x (or p = r + beta p), forward, half spectrum
-    TRowsFwdOp a{{}, x, cg ? const_cast<float*>(x) : nullptr, cg_r, cg, w.t1, w.tw_2n, N * N, N};
+    TRowsFwdOp a{{}, x, cg ? const_cast<float*>(x) : nullptr, cg_r, cg, w.t1, w.tw_2n, N * N, N, cg_z};
     if ((e = cudaFuncSetAttribute(k_rows_cg<L, TRowsFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
         return e;
     k_rows_cg<L, TRowsFwdOp><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(a, cg);
@@ -536,9 +538,251 @@ static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg) {
-    FIRM_SWITCH_2N(2 * P.N, { return toeplitz_l<LL>(P, x, y, lam, cg_r, cg); });
+cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg,
+                            const float* cg_z) {
+    FIRM_SWITCH_2N(2 * P.N, { return toeplitz_l<LL>(P, x, y, lam, cg_r, cg, cg_z); });
     return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioner z = F^-1 diag(d) F r on the N^3 grid (PCG; the benchmark spec).  Five
+// passes like the Toeplitz apply without padding: real rows forward (half
+// spectrum), y forward, z forward x d x z inverse, y inverse, Hermitian rows
+// inverse with <r, z> reduced and beta = <r,z>_new / <r,z>_old set on the device.
+// d already holds the 1/N^3 of the inverse transform.
+// ---------------------------------------------------------------------------
+#define FIRM_SWITCH_N(Nval, ...)                                                              \
+    switch (Nval) {                                                                          \
+        FIRM_CASE_L(16, __VA_ARGS__) FIRM_CASE_L(32, __VA_ARGS__) FIRM_CASE_L(48, __VA_ARGS__)   \
+        FIRM_CASE_L(64, __VA_ARGS__) FIRM_CASE_L(96, __VA_ARGS__) FIRM_CASE_L(128, __VA_ARGS__)  \
+        default: return cudaErrorInvalidValue;                                               \
+    }
+
+struct PRowsFwdOp : NoFinish {
+    const double* r; float2* u; const float2* tw; int n_rows, N;
+    __device__ __forceinline__ float2 load(int row, int n) const {
+        return make_float2((float)__ldg(&r[(size_t)row * N + n]), 0.0f);
+    }
+    __device__ __forceinline__ void store(int row, int k, float2 v) const {
+        if (k <= N / 2) u[(size_t)row * (N / 2 + 1) + k] = v;
+    }
+};
+struct PColsYOp {
+    float2* u; const float2* tw; int n_outer, n_inner, N;
+    __device__ __forceinline__ float2 load(int o, int n, int i) const { return u[((size_t)o * N + n) * n_inner + i]; }
+    __device__ __forceinline__ void store(int o, int k, int i, float2 v) const { u[((size_t)o * N + k) * n_inner + i] = v; }
+};
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_pc_z(float2* __restrict__ u, const float* __restrict__ d,
+                                                   const float2* __restrict__ tw, int n_inner, const CgState* cg) {
+    extern __shared__ float2 S[];
+    if (cg->done) return;
+    const int c0 = blockIdx.x * kTX;
+    const int nl = min(kTX, n_inner - c0);
+    auto ld = [&](int line, int n) { return u[(size_t)n * n_inner + c0 + line]; };
+    auto mul = [&](int line, int k) { return __ldg(&d[(size_t)k * n_inner + c0 + line]); };
+    auto st = [&](int line, int n, float2 v) { u[(size_t)n * n_inner + c0 + line] = v; };
+    block_fft_mul_ifft<L>(nl, ld, mul, st, S, tw);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restrict__ u, const double* __restrict__ r,
+                                                          float* __restrict__ z, double* red, CgState* cg,
+                                                          const float2* __restrict__ tw, int n_rows) {
+    // z <- P r; reduces <r, z_new> and <r, z_old> for the flexible (Polak-Ribiere)
+    // beta = (<r,z_new> - <r,z_old>) / <r_old,z_old>, which tolerates the FP32 rounding
+    // of the preconditioner apply.
+    extern __shared__ float2 S[];
+    __shared__ double s_red[2][kThreads / 32];
+    __shared__ double s_fin[2][kThreads];
+    __shared__ bool s_last;
+    if (cg->done) return;
+    constexpr int N = L, H = L / 2 + 1;
+    constexpr int ROWS = rows_per_block<L>();
+    const int r0 = blockIdx.x * ROWS;
+    const int nl = min(ROWS, n_rows - r0);
+    double acc = 0.0, acc_old = 0.0;
+    auto ld = [&](int line, int n) {
+        const float2* row = u + (size_t)(r0 + line) * H;
+        return n <= N / 2 ? row[n] : c_conj(row[N - n]);
+    };
+    auto st = [&](int line, int k, float2 v) {
+        const size_t i = (size_t)(r0 + line) * N + k;
+        const double ri = __ldg(&r[i]);
+        acc_old += ri * (double)z[i];
+        z[i] = v.x;
+        acc += ri * (double)v.x;
+    };
+    block_fft<L, +1, false>(nl, ld, st, S, tw);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        acc_old += __shfl_down_sync(0xffffffffu, acc_old, o);
+    }
+    if ((threadIdx.x & 31) == 0) { s_red[0][threadIdx.x >> 5] = acc; s_red[1][threadIdx.x >> 5] = acc_old; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b0 = 0.0, b1 = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) { b0 += s_red[0][i]; b1 += s_red[1][i]; }
+        red[2 * blockIdx.x] = b0;
+        red[2 * blockIdx.x + 1] = b1;
+        __threadfence();
+        const unsigned t = atomicAdd(&cg->ticket_c, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double v0 = 0.0, v1 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        v0 += ((volatile double*)red)[2 * i];
+        v1 += ((volatile double*)red)[2 * i + 1];
+    }
+    s_fin[0][threadIdx.x] = v0;
+    s_fin[1][threadIdx.x] = v1;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            s_fin[0][threadIdx.x] += s_fin[0][threadIdx.x + s];
+            s_fin[1][threadIdx.x] += s_fin[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double rz_new = s_fin[0][0], rz_old_new_r = s_fin[1][0];
+        cg->beta = cg->first ? 0.0 : fmax(0.0, (rz_new - rz_old_new_r) / cg->rz);
+        cg->rz = rz_new;
+        cg->first = 0;
+        cg->ticket_c = 0;
+        if (!(rz_new > 0.0) || !isfinite(rz_new)) {     // P must be positive definite
+            if (!(rz_new == 0.0)) cg->status = FIRM_EBREAKDOWN;
+            cg->done = 1;
+        }
+    }
+}
+
+template <int L>
+static cudaError_t precond_l(Plan& P, const double* r, float* z, CgState* cg) {
+    Workspace& w = P.ws;
+    constexpr int N = L, H = L / 2 + 1;
+    constexpr int ROWS = rows_per_block<L>();
+    const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
+    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
+    float2* u = w.t1;                       // N x N x (N/2+1) complex
+    cudaError_t e;
+    PRowsFwdOp a{{}, r, u, w.tw_n, N * N, N};
+    if ((e = cudaFuncSetAttribute(k_rows_cg<L, PRowsFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+        return e;
+    k_rows_cg<L, PRowsFwdOp><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(a, cg);
+    PColsYOp b{u, w.tw_n, N, H, N};
+    const int tiles = (H + kTX - 1) / kTX;
+    if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, PColsYOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+        return e;
+    k_cols_cg<L, -1, PColsYOp><<<N * tiles, kThreads, smem_cols, P.stream>>>(b, cg);
+    const int n_inner = N * H;
+    if ((e = cudaFuncSetAttribute(k_pc_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols))) return e;
+    k_pc_z<L><<<(n_inner + kTX - 1) / kTX, kThreads, smem_cols, P.stream>>>(u, w.pc_diag, w.tw_n, n_inner, cg);
+    if ((e = cudaFuncSetAttribute(k_cols_cg<L, +1, PColsYOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+        return e;
+    k_cols_cg<L, +1, PColsYOp><<<N * tiles, kThreads, smem_cols, P.stream>>>(b, cg);
+    if ((e = cudaFuncSetAttribute(k_pc_rows_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+        return e;
+    k_pc_rows_inv<L><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(u, r, z, w.red_a, cg, w.tw_n, N * N);
+    P.launches += 5;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precond(Plan& P, const double* r, float* z, CgState* cg) {
+    FIRM_SWITCH_N(P.N, { return precond_l<LL>(P, r, z, cg); });
+    return cudaErrorInvalidValue;
+}
+
+// T. Chan's optimal circulant of the Toeplitz operator (the circulant nearest to it in
+// Frobenius norm): column c(m) = sum over n = m (mod N), n in (-N, N)^3, of
+// Ker(n) prod_a (N - |n_a|) / N, read from the Ker half box (Ker(-n) = Ker(n)).
+__global__ void k_chan_column(const float* __restrict__ ker, double* __restrict__ c, int N) {
+    const long long total = (long long)N * N * N;
+    const int N2 = 2 * N;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int m1 = (int)(i % N), m2 = (int)((i / N) % N), m3 = (int)(i / ((long long)N * N));
+        double acc = 0.0;
+        for (int a = 0; a < 2; ++a) {
+            if (a && m1 == 0) continue;                 // n1 = -N: weight 0
+            const int n1 = m1 - a * N;
+            const double w1 = (double)(N - abs(n1)) / N;
+            for (int b = 0; b < 2; ++b) {
+                if (b && m2 == 0) continue;
+                const int n2 = m2 - b * N;
+                const double w2 = w1 * (double)(N - abs(n2)) / N;
+                for (int d = 0; d < 2; ++d) {
+                    if (d && m3 == 0) continue;
+                    const int n3 = m3 - d * N;
+                    const double w3 = w2 * (double)(N - abs(n3)) / N;
+                    const size_t idx = n1 >= 0 ? ((size_t)(n3 + N) * N2 + (n2 + N)) * (N + 1) + n1
+                                               : ((size_t)(N - n3) * N2 + (N - n2)) * (N + 1) + (-n1);
+                    acc += w3 * (double)__ldg(&ker[idx]);
+                }
+            }
+        }
+        c[i] = acc;
+    }
+}
+
+struct PColsZOp {
+    float2* u; const float2* tw; int n_outer, n_inner;
+    __device__ __forceinline__ float2 load(int, int n, int i) const { return u[(size_t)n * n_inner + i]; }
+    __device__ __forceinline__ void store(int, int k, int i, float2 v) const { u[(size_t)k * n_inner + i] = v; }
+};
+
+// d = 1 / ((max(kappa, 0) + floor) N^3), floor = lam_eff or 1e-6 kappa(0)
+__global__ void k_pc_diag(const float2* __restrict__ u, float* __restrict__ d, long long total, float lam) {
+    const float floor_v = lam > 0.0f ? lam : 1e-6f * fmaxf(u[0].x, 1e-30f);
+    const float n3 = (float)d[total];   // N^3 stashed past the end by the launcher
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+        d[i] = 1.0f / ((fmaxf(u[i].x, 0.0f) + floor_v) * n3);
+}
+
+template <int L>
+static cudaError_t chan_spectrum_l(Plan& P) {
+    Workspace& w = P.ws;
+    constexpr int N = L, H = L / 2 + 1;
+    constexpr int ROWS = rows_per_block<L>();
+    const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
+    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
+    float2* u = w.t1;
+    cudaError_t e;
+    k_chan_column<<<P.num_sms * 4, 256, 0, P.stream>>>(w.ker, w.r, N);
+    PRowsFwdOp a{{}, w.r, u, w.tw_n, N * N, N};
+    if ((e = cudaFuncSetAttribute(k_rows_cg<L, PRowsFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+        return e;
+    k_rows_cg<L, PRowsFwdOp><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(a, nullptr);
+    PColsYOp b{u, w.tw_n, N, H, N};
+    if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, PColsYOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+        return e;
+    k_cols_cg<L, -1, PColsYOp><<<N * ((H + kTX - 1) / kTX), kThreads, smem_cols, P.stream>>>(b, nullptr);
+    PColsZOp c{u, w.tw_n, 1, N * H};
+    if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, PColsZOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+        return e;
+    k_cols_cg<L, -1, PColsZOp><<<(N * H + kTX - 1) / kTX, kThreads, smem_cols, P.stream>>>(c, nullptr);
+    P.launches += 4;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chan_spectrum(Plan& P) {
+    FIRM_SWITCH_N(P.N, { return chan_spectrum_l<LL>(P); });
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pc_build_circulant(Plan& P) {
+    const long long total = (long long)P.N * P.N * (P.N / 2 + 1);
+    const float n3 = (float)P.N * (float)P.N * (float)P.N;
+    cudaError_t e = cudaMemcpyAsync(P.ws.pc_diag + total, &n3, sizeof(float), cudaMemcpyHostToDevice, P.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
+    if (e != cudaSuccess) return e;
+    k_pc_diag<<<P.num_sms * 4, 256, 0, P.stream>>>(P.ws.t1, P.ws.pc_diag, total, (float)P.lam_eff);
+    P.launches += 1;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -44,6 +44,11 @@ struct CgState {
     int done;         // 1: stop (converged, max_iter or breakdown)
     int status;       // firm_status of the solve
     unsigned int ticket_a, ticket_b;   // last-block counters of the two reductions
+    double rz;        // <r, z> with z = P r (preconditioned solve)
+    int use_pc;       // 1: preconditioned CG
+    int first;        // 1 until the first preconditioner application
+    unsigned int ticket_c;
+    int pad_;
 };
 
 struct Workspace {
@@ -85,6 +90,12 @@ struct Workspace {
     float* q = nullptr;
     float2* t1 = nullptr;           // N x N x (N+1)
     float2* t2 = nullptr;           // N x 2N x (N+1)
+    float* z = nullptr;             // preconditioned residual (N^3)
+    float* pc_diag = nullptr;       // preconditioner, Fourier diagonal N x N x (N/2+1)
+    float* pc_feat = nullptr;       // 1024-bin density histogram
+    float* pc_table = nullptr;      // 1024-bin log table of the TABLE / BINNED preconditioner
+    double* pc_s1 = nullptr;        // per-bin sums for the binned target
+    double* pc_s2 = nullptr;
     double* red_a = nullptr;        // partial sums
     double* red_b = nullptr;
     double* hist = nullptr;
@@ -112,6 +123,11 @@ struct Plan {
     double cg_iters = 0;
     int num_sms = 0;
     long long launches = 0;         // kernels launched by this plan
+    int pc_mode = 0;                // FIRM_PRECOND_*
+    bool pc_ready = false;          // pc_diag built for the current K-hat and mode
+    float pc_axis[3] = {0, 0, 1};   // principal viewing axis of the last firm_kernel
+    float ker0 = 1.0f;              // Ker(0) of the last firm_kernel
+    int last_M = 0;                 // images of the last firm_kernel
     // device pointers of the current call's inputs (caller's or staged copies)
     const double* cur_R = nullptr;
     const double* cur_shifts = nullptr;
@@ -143,10 +159,23 @@ cudaError_t launch_khat(Plan& P);              // Ker -> K-hat
 cudaError_t launch_rhs_transform(Plan& P);     // grid -> A*b
 // Toeplitz apply y = Ker * x + lam x.  With cg != nullptr the first pass forms
 // p = r + beta p in place (x = p, r given) and the last pass reduces <p, y>.
-cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg);
+cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg,
+                            const float* cg_z = nullptr);
+
+// Preconditioner: z = P r through N^3 FFTs with the Fourier diagonal pc_diag; the last
+// pass reduces <r, z> and sets beta (fft_passes.cu).
+cudaError_t launch_precond(Plan& P, const double* r, float* z, CgState* cg);
+cudaError_t launch_chan_spectrum(Plan& P);       // T. Chan circulant spectrum into ws.t1 (half spectrum)
+cudaError_t launch_pc_build_circulant(Plan& P);  // pc_diag = 1 / ((kappa + lam_eff) N^3) from ws.t1
+
+// ---- launchers (lpre.cu) ----
+cudaError_t launch_view_axis(Plan& P, const double* R, int M);
+cudaError_t launch_pc_features(Plan& P, int M, float* hist);
+cudaError_t launch_pc_target_sums(Plan& P, double* s1, double* s2);
+cudaError_t launch_pc_from_table(Plan& P, const float* table);
 
 // ---- launchers (cg.cu) ----
-cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_tol);
+cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_tol, bool use_pc);
 cudaError_t launch_cg_update(Plan& P);
 
 }  // namespace firm

@@ -1,0 +1,140 @@
+"""Learned Fourier-domain CG preconditioner: training data from the method itself, training
+and inference through the C ABI (firm_pc_features, firm_pc_target, firm_mlp_*).
+
+Training set: kernels the method generates at N = 64 from random orientation mixtures
+(Haar, von Mises--Fisher about 1-3 axes, polar caps), 500-3000 images, 1-4 of 8 defocus
+groups; each sample is the per-bin density feature vector and the per-bin least-squares
+target of the circulant preconditioner.  The network (1024 -> 256 -> 256 -> 1024) maps
+log-density to the log table; the plan then uses exp(table) / Ker(0) as the Fourier
+diagonal (FIRM_PRECOND_TABLE).  Python only marshals arguments and draws the seeded
+random numbers (initial weights, mini-batch indices, orientations); every arithmetic
+step runs in libfirm.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import synth
+
+from . import _lib as L
+from .recon import Reconstructor
+
+NBINS = 1024
+DEFOCUS_UM = np.linspace(1.0, 3.5, 8)
+
+
+def random_rotations(M: int, rng: np.random.Generator) -> np.ndarray:
+    """A random mixture of Haar, von Mises--Fisher and polar-cap view distributions."""
+    kinds = rng.dirichlet(np.ones(3))
+    n = (kinds * M).astype(int)
+    n[0] += M - n.sum()
+    parts = [synth.haar_rotations(n[0], rng)]
+    if n[1] > 0:
+        parts.append(synth.mixed_rotations(n[1], rng, frac_vmf=1.0, kappa=float(rng.uniform(5, 60)),
+                                           n_axes=int(rng.integers(1, 4))))
+    if n[2] > 0:
+        pole = rng.standard_normal(3)
+        parts.append(synth.cap_rotations(n[2], float(rng.uniform(10, 40)), pole, rng))
+    R = np.concatenate(parts)
+    return R[rng.permutation(M)]
+
+
+def net_input(feat: np.ndarray) -> np.ndarray:
+    """x_b = log(1024 f_b + 1e-3)."""
+    return np.log(NBINS * np.asarray(feat, np.float64) + 1e-3).astype(np.float32)
+
+
+def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3000), device="cuda:0"):
+    """(X, T): network inputs and targets of n_kernels method-generated kernels."""
+    rng = np.random.default_rng(seed)
+    groups = synth.ctf_group_table(DEFOCUS_UM)
+    rec = Reconstructor(N, m_range[1], groups=groups, W=6, lam=1e-3, device=device)
+    X = np.empty((n_kernels, NBINS), np.float32)
+    T = np.empty((n_kernels, NBINS), np.float32)
+    f = np.empty(NBINS, np.float32)
+    t = np.empty(NBINS, np.float32)
+    for i in range(n_kernels):
+        M = int(rng.integers(m_range[0], m_range[1] + 1))
+        R = random_rotations(M, rng)
+        sub = rng.choice(len(DEFOCUS_UM), int(rng.integers(1, 5)), replace=False)
+        gid = sub[rng.integers(0, len(sub), M)].astype(np.int32)
+        rec.kernel(np.ascontiguousarray(R.reshape(M, 9)), gid, M=M)
+        rec.pc_features(f)
+        rec.pc_target(t)
+        X[i] = net_input(f)
+        T[i] = t
+    rec.close()
+    return X, T
+
+
+def init_params(seed: int = 52) -> np.ndarray:
+    """He-normal weights, zero biases, in the firm_mlp parameter layout."""
+    rng = np.random.default_rng(seed)
+    w = (NBINS, 256, 256, NBINS)
+    out = []
+    for i in range(3):
+        out.append((rng.standard_normal((w[i + 1], w[i])) * np.sqrt(2.0 / w[i])).astype(np.float32).ravel())
+        out.append(np.zeros(w[i + 1], np.float32))
+    p = np.concatenate(out)
+    assert p.size == L.firm_mlp_param_count()
+    return p
+
+
+def train(X: np.ndarray, T: np.ndarray, steps: int = 3000, batch: int = 64, lr: float = 1e-3, seed: int = 53,
+          device="cuda:0", log_every: int = 500):
+    """Adam on the mean squared error; returns (params on the device, loss history)."""
+    dev = torch.device(device)
+    rng = np.random.default_rng(seed)
+    params = torch.from_numpy(init_params(seed - 1)).to(dev)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    g = torch.empty_like(params)
+    Xd = torch.from_numpy(X).to(dev)
+    Td = torch.from_numpy(T).to(dev)
+    work = torch.empty(L.firm_mlp_work_floats(batch), dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    hist = []
+    for step in range(1, steps + 1):
+        idx = torch.from_numpy(rng.integers(0, X.shape[0], batch)).to(dev)
+        xb = Xd.index_select(0, idx).contiguous()
+        tb = Td.index_select(0, idx).contiguous()
+        L.firm_mlp_grad(params, batch, xb, tb, g, work, loss, s)
+        L.firm_mlp_adam(params, g, m, v, step, lr, s)
+        if step % log_every == 0 or step == 1:
+            hist.append((step, float(loss.item())))
+    return params, hist
+
+
+def evaluate(params: torch.Tensor, X: np.ndarray, T: np.ndarray, bf16: bool = False) -> float:
+    """Mean squared error of the network on (X, T)."""
+    y = predict(params, X, bf16=bf16)
+    return float(((y - T) ** 2).mean())
+
+
+def predict(params: torch.Tensor, X: np.ndarray, bf16: bool = True) -> np.ndarray:
+    """Network output (log tables) for rows of X; BF16 weights by default (inference)."""
+    dev = params.device
+    n = X.shape[0]
+    x = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    y = torch.empty((n, NBINS), dtype=torch.float32, device=dev)
+    work = torch.empty(L.firm_mlp_work_floats(n), dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    if bf16:
+        pb = torch.empty(params.numel(), dtype=torch.bfloat16, device=dev)
+        L.firm_mlp_to_bf16(params, pb, s)
+        L.firm_mlp_forward_bf16(pb, params, n, x, y, work, s)
+    else:
+        L.firm_mlp_forward(params, n, x, y, work, s)
+    torch.cuda.synchronize(dev)
+    return y.cpu().numpy()
+
+
+def apply_learned(rec: Reconstructor, params: torch.Tensor, bf16: bool = True) -> np.ndarray:
+    """Features of the plan's last kernel -> network -> FIRM_PRECOND_TABLE.  Returns the table."""
+    f = np.empty(NBINS, np.float32)
+    rec.pc_features(f)
+    table = predict(params, net_input(f)[None], bf16=bf16)[0]
+    rec.set_precond_table(np.ascontiguousarray(table))
+    return table

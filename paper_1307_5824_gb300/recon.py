@@ -42,6 +42,21 @@ class Reconstructor:
     def toeplitz_apply(self, x, y):
         L.firm_toeplitz_apply(self.plan, x, y)
 
+    def set_precond(self, mode: int):
+        L.firm_set_precond(self.plan, mode)
+
+    def set_precond_table(self, table_log):
+        L.firm_set_precond_table(self.plan, table_log)
+
+    def pc_features(self, out):
+        L.firm_pc_features(self.plan, out)
+
+    def pc_target(self, out):
+        L.firm_pc_target(self.plan, out)
+
+    def pc_axis(self):
+        return L.firm_pc_axis(self.plan)
+
     def lambda_eff(self) -> float:
         return L.firm_lambda_eff(self.plan)
 

@@ -208,3 +208,67 @@ def test_bad_arguments_are_rejected(F):
         rec.kernel(np.zeros((M + 1, 9)), M=M + 1)
     assert e.value.code == F._lib.FIRM_EINVAL
     rec.close()
+
+
+def test_repeated_calls_agree(F):
+    """Same inputs, same plan, three calls: Ker, A*b and the CG iterate agree to FP32
+    rounding (the only run-to-run freedom is the order of FP32/FP64 additions)."""
+    inp = synth.config_inputs("C1")
+    N, M = inp["N"], inp["M"]
+    rec = F.Reconstructor(N, M, W=7, lam=0.0)
+    R = _dev(inp["R"].reshape(M, 9))
+    img = _dev(inp["images"])
+    sh = _dev(inp["shifts"])
+    outs = []
+    for _ in range(3):
+        rec.kernel(R)
+        rec.backproject(img, sh, R)
+        ker = torch.empty(rec.half_shape(), dtype=torch.float32, device="cuda")
+        rhs = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+        rec.copy_out(F._lib.FIRM_OUT_KER, ker)
+        rec.copy_out(F._lib.FIRM_OUT_RHS, rhs)
+        x = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+        rec.cg_solve(x, 10)
+        torch.cuda.synchronize()
+        outs.append((ker.cpu().numpy(), rhs.cpu().numpy(), x.cpu().numpy()))
+    for name, i in (("Ker", 0), ("A*b", 1), ("x10", 2)):
+        d = max(rel(o[i], outs[0][i]) for o in outs[1:])
+        print(f"repeat {name}: max rel diff {d:.3e}")
+        assert d <= (1e-6 if i < 2 else 2e-5), (name, d)
+
+
+def test_preconditioned_cg_matches_oracle(F):
+    """PCG with the circulant preconditioner (K-hat at even frequencies): the GPU iterate
+    after 8 iterations matches the oracle's PCG iterate; to rel-res 1e-4 it needs fewer
+    iterations than plain CG and its true residual meets the tolerance."""
+    N, M = 32, 150
+    inp = _inputs("C2", N, M)
+    K, h = _oracle_h(inp)
+    rec = F.Reconstructor(N, M, groups=inp["groups"], W=7, lam=1e-3)
+    R = _dev(inp["R"].reshape(M, 9))
+    g = _dev(inp["group_id"])
+    rec.kernel(R, g)
+    rec.backproject(_dev(inp["images"]), _dev(inp["shifts"]), R, g)
+    rec.set_precond(F._lib.FIRM_PRECOND_CIRCULANT)
+    x = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    rec.cg_solve(x, 8)
+    torch.cuda.synchronize()
+    Ker = O.kernel(inp["R"], h, K, N).real
+    rhs = O.backproject(inp["images"].astype(np.float64), inp["shifts"], inp["R"], h, K)
+    lam = O.lambda_eff(1e-3, 0, Ker[N, N, N])
+    Kh = O.khat(Ker).real
+    op = lambda v: O.toeplitz_apply(Kh, v, lam).real
+    Pc = O.circulant_preconditioner(O.wrapped_spectrum(Ker), lam)
+    xo, _, _ = O.cg(op, rhs, 8, precond=Pc)
+    err = rel(x.cpu().numpy(), xo)
+    print(f"PCG 8 iterations: rel err vs oracle {err:.3e}")
+    assert err <= 1e-4
+    st, it_pc = rec.cg_solve(x, 500, rel_tol=1e-4)
+    rec.set_precond(F._lib.FIRM_PRECOND_NONE)
+    x2 = torch.empty_like(x)
+    st2, it_plain = rec.cg_solve(x2, 500, rel_tol=1e-4)
+    torch.cuda.synchronize()
+    print(f"iterations to rel-res 1e-4: plain {it_plain}, circulant {it_pc}")
+    assert st == 0 and st2 == 0 and it_pc < it_plain
+    true_res = np.linalg.norm(op(x.cpu().numpy().astype(np.float64)) - rhs) / np.linalg.norm(rhs)
+    assert true_res <= 3e-4

@@ -338,3 +338,145 @@ def test_cg_recovers_blob_phantom_from_dense_noiseless_views():
     rhs_b = O.adjoint(O.forward(Vb, R, h, K), R, h, K, N).real
     xb, _, _ = O.cg(op, rhs_b, 500)
     assert np.linalg.norm(xb - Vb) / np.linalg.norm(Vb) <= 5e-5
+
+
+def test_wrapped_spectrum_is_khat_at_even_frequencies():
+    """The 2N-point DFT of the circulant column at frequency 2k equals the N-point DFT of
+    the column wrapped onto N (a DFT identity), so K-hat(2k) is the spectrum of the
+    wrapped circulant used as preconditioner."""
+    N, M = 8, 5
+    K = O.disc(N)
+    R = _rand_rot(M, 23)
+    h = O.ctf_weights(N, K, _groups(), np.arange(M) % 2)
+    Ker = O.kernel(R, h, K, N)
+    kap = O.wrapped_spectrum(Ker, weighted=False)
+    Kh = O.khat(Ker).real
+    np.testing.assert_allclose(kap, Kh[::2, ::2, ::2], atol=1e-10 * abs(Kh).max())
+
+
+def test_chan_circulant_is_the_frobenius_projection():
+    """T. Chan's circulant is the orthogonal projection of the Toeplitz matrix (eq. toep3)
+    onto circulants: its column m is the mean of T over the wrapped diagonal i - j = m
+    (mod N).  Checked against the explicit N^3 x N^3 matrix at N = 4; its spectrum is
+    positive for the positive semidefinite A*A."""
+    N, M = 4, 6
+    K = O.disc(N)
+    R = _rand_rot(M, 26)
+    h = O.ctf_weights(N, K, _groups(), np.arange(M) % 2)
+    Ker = O.kernel(R, h, K, N).real
+    n = np.stack(np.meshgrid(*(np.arange(N),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    d = n[:, None, :] - n[None, :, :]
+    T = Ker[d[..., 0] + N, d[..., 1] + N, d[..., 2] + N]
+    key = ((d % N) * np.array([N * N, N, 1])).sum(-1)
+    c = np.bincount(key.ravel(), T.ravel(), N ** 3) / np.bincount(key.ravel(), None, N ** 3)
+    ref = np.fft.fftn(c.reshape(N, N, N)).real
+    kap = O.wrapped_spectrum(Ker)
+    np.testing.assert_allclose(kap, ref, atol=1e-10 * abs(ref).max())
+    assert kap.min() > -1e-10 * kap.max()
+
+
+def test_preconditioned_cg_delta_kernel_one_step_and_matches_plain_cg():
+    """With a delta kernel the operator is (c + lam) I and the circulant preconditioner is
+    its exact inverse: one PCG step.  On a real kernel PCG and plain CG reach the same
+    solution (the dense solve at N = 4)."""
+    N = 4
+    Ker = np.zeros((2 * N,) * 3)
+    Ker[N, N, N] = 3.0
+    Kh = O.khat(Ker).real
+    rng = np.random.default_rng(24)
+    b = rng.standard_normal((N,) * 3)
+    P = O.circulant_preconditioner(O.wrapped_spectrum(Ker), 0.5)   # delta kernel: all weights 1 at n=0
+    x, hist, it = O.cg(lambda v: O.toeplitz_apply(Kh, v, 0.5).real, b, 10, rel_tol=1e-12, precond=P)
+    assert it == 1
+    np.testing.assert_allclose(x, b / 3.5, rtol=1e-12)
+    K = O.disc(N)
+    R = _rand_rot(6, 25)
+    h = O.ctf_weights(N, K, _groups(), np.arange(6) % 2)
+    Ker = O.kernel(R, h, K, N).real
+    lam = O.lambda_eff(1e-2, 0, Ker[N, N, N])
+    Kh = O.khat(Ker).real
+    op = lambda v: O.toeplitz_apply(Kh, v, lam).real
+    n = np.stack(np.meshgrid(*(np.arange(N),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    d = n[:, None, :] - n[None, :, :] + N
+    T = Ker[d[..., 0], d[..., 1], d[..., 2]] + lam * np.eye(N ** 3)
+    ref = np.linalg.solve(T, b.reshape(-1)).reshape((N,) * 3)
+    P = O.circulant_preconditioner(O.wrapped_spectrum(Ker), lam)
+    x, _, it_pc = O.cg(op, b, 200, rel_tol=1e-13, precond=P)
+    np.testing.assert_allclose(x, ref, atol=1e-9 * abs(ref).max())
+
+
+# -- learned preconditioner (oracle/lpre.py) -------------------------------------------
+
+from oracle import lpre as LP   # noqa: E402
+
+
+def _small_params(seed):
+    rng = np.random.default_rng(seed)
+    sizes = LP.WIDTHS
+    params = []
+    for i in range(3):
+        params.append(rng.standard_normal((sizes[i + 1], sizes[i])) / np.sqrt(sizes[i]))
+        params.append(0.1 * rng.standard_normal(sizes[i + 1]))
+    return params
+
+
+def test_mlp_gradient_matches_finite_differences():
+    """Backward pass of the preconditioner network against central differences of the loss."""
+    params = _small_params(30)
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal((3, LP.NBINS))
+    t = rng.standard_normal((3, LP.NBINS))
+    loss, grads = LP.mlp_loss_grad(params, x, t)
+    eps = 1e-6
+    for layer in range(6):
+        p = params[layer]
+        for _ in range(4):
+            idx = tuple(rng.integers(0, s) for s in p.shape)
+            old = p[idx]
+            p[idx] = old + eps
+            lp, _ = LP.mlp_loss_grad(params, x, t)
+            p[idx] = old - eps
+            lm, _ = LP.mlp_loss_grad(params, x, t)
+            p[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - grads[layer][idx]) <= 1e-6 * max(1e-3, abs(fd)) + 1e-10
+
+
+def test_adam_first_step_closed_form():
+    """From zero moments the bias-corrected first Adam step is -lr * g / (|g| + eps)."""
+    p = [np.array([1.0, -2.0, 3.0])]
+    g = [np.array([0.5, -4.0, 0.0])]
+    m, v = [np.zeros(3)], [np.zeros(3)]
+    LP.adam_step(p, g, m, v, 1, 0.01)
+    np.testing.assert_allclose(p[0], [1.0 - 0.01, -2.0 + 0.01, 3.0], atol=1e-7)
+
+
+def test_target_of_constant_spectrum_and_table_round_trip():
+    """kappa = c everywhere: every bin's least-squares multiplier is 1 / (c + lam), so
+    t_b = log(Ker(0) / (c + lam)) and the expanded diagonal is 1 / (c + lam)."""
+    N, c, lam, ker0 = 8, 5.0, 0.5, 7.0
+    a = np.array([0.0, 0.0, 1.0])
+    t = LP.target(np.full((N, N, N), c), lam, ker0, a)
+    np.testing.assert_allclose(t, np.log(ker0 / (c + lam)), rtol=1e-12)
+    d = LP.table_diagonal(t, N, ker0, a)
+    np.testing.assert_allclose(d, 1.0 / (c + lam), rtol=1e-12)
+
+
+def test_features_sum_to_one_and_identity_rotation_lies_in_cone_zero():
+    """All slices of R = I lie in the plane q3 = 0, perpendicular to the viewing axis e3:
+    the density is in cone 0, and its shell profile is the h^2-weighted count of disc
+    points per |k| ring (computed directly)."""
+    N, M = 16, 3
+    K = O.disc(N)
+    R = np.repeat(np.eye(3)[None], M, 0)
+    h = O.ctf_weights(N, K, _groups(), np.arange(M) % 2)
+    a = LP.principal_axis(R)
+    np.testing.assert_allclose(np.abs(a), [0, 0, 1], atol=1e-12)
+    f = LP.features(R, h, K, N, a).reshape(LP.SHELLS, LP.CONES)
+    assert abs(f.sum() - 1.0) < 1e-12
+    assert np.all(f[:, 1:] == 0)
+    r = np.sqrt((K ** 2).sum(1))
+    shell = np.minimum(63, np.floor(64 * r / (N / 2))).astype(int)
+    ref = np.zeros(64)
+    np.add.at(ref, shell, (h * h).sum(0))
+    np.testing.assert_allclose(f[:, 0], ref / ref.sum(), rtol=1e-12)
