@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--N", type=int, default=None, help="override volume edge (profiling of smaller cases)")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER, help="CG iteration cap (profiling)")
     ap.add_argument("--W", type=int, default=6)
-    ap.add_argument("--precond", default="none", choices=["none", "circulant", "binned", "learned"])
+    ap.add_argument("--precond", default="learned", choices=["none", "circulant", "binned", "learned"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-CG comparison run")
     ap.add_argument("--train-kernels", type=int, default=2000, help="N=64 kernels the learned preconditioner trains on")
     ap.add_argument("--workload", default="C3", choices=["C3", "C5"],
                     help="C3: 50k Haar views, 20 groups; C5: 40k views 85%% in a 15 degree cap, 8 groups")
@@ -306,6 +307,31 @@ def main():
         e2e = {"value": e2e_s, "unit": "s/recon", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(x_h.numel() * 4)}
 
+    # the same reconstruction with plain CG (the comparison the metric names)
+    plain = None
+    if not args.no_compare and args.precond != "none":
+        net_saved = net
+        net = None
+        rec.set_precond(L.FIRM_PRECOND_NONE)
+        for _ in range(2):
+            st, it_pl = step(R, gid, sh, img, x)
+        torch.cuda.synchronize(dev)
+        rec.set_timing(True)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        it_plain = []
+        cg_plain = 0.0
+        p0.record(stream)
+        for _ in range(args.steps):
+            st, it_pl = step(R, gid, sh, img, x)
+            it_plain.append(it_pl)
+            cg_plain += rec.stage_times()["cg"]
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        rec.set_timing(False)
+        plain = {"s_per_recon": p0.elapsed_time(p1) / args.steps / 1e3, "cg_iters": int(np.median(it_plain)),
+                 "cg_ms": cg_plain / args.steps}
+        net = net_saved
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -344,8 +370,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "N=128 volume, 50000 BF16 128x128 images (60-blob phantom, Haar views, "
                                "20 defocus groups, SNR 0.05), KB W=%d sigma=2, lambda=1e-3 x Ker(0), "
-                               "plain CG to rel-res 1e-4" % W,
-                   "N": N, "M": M, "W": W, "precond": "none",
+                               "%s-preconditioned CG to rel-res 1e-4" % (W, args.precond),
+                   "N": N, "M": M, "W": W, "precond": args.precond,
                    "l2": "inputs larger than L2: 1.64 GB BF16 images read and a 1.07 GB FP64 fine grid "
                          "written every step"},
         "spread_gpts_per_s": pts / (spread_ms * 1e-3) / 1e9,
@@ -364,6 +390,7 @@ def main():
         "synth_s": round(t_syn, 1),
         "precond": args.precond,
         "learned_training": train_info,
+        "plain_cg": plain,
     }
     print(json.dumps(out))
     if world > 1:

@@ -168,7 +168,6 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.count = c.take<uint32_t>(nb3);
     w.cursor = c.take<uint32_t>(nb3);
     w.work = c.take<int4>(max_work);
-    w.class_off = c.take<uint32_t>(max_work * 32);
     w.counters = c.take<int>(8);
     const size_t grid_bytes = std::max(Gk * Gk * Gk * sizeof(double), Gr * Gr * Gr * 2 * sizeof(double));
     w.grid = c.take<double>(grid_bytes / sizeof(double));

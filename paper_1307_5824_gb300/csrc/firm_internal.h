@@ -73,7 +73,6 @@ struct Workspace {
     uint32_t* cursor = nullptr;
     uint32_t* payload = nullptr;    // point ids m * nH + t sorted by brick, then bank class
     uint8_t* cls = nullptr;         // bank class of each binned point
-    uint32_t* class_off = nullptr;  // per work item, offset of each bank class
     int4* work = nullptr;           // (brick, start, count, -)
     int* counters = nullptr;        // [0] work items, [1] work cursor, [2] error flag
     double* grid = nullptr;         // fine grid, FP64 (real for Ker, complex for A*b)

@@ -237,42 +237,76 @@ __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__
     }
 }
 
-// Counting sort of each piece by bank class, in place; class_off[item * 32 + c] is the
-// offset of class c inside the piece.
+// Orders each piece round-robin over bank classes, in place: the point of rank r in
+// class c (order within a class is arbitrary) goes to position A(r) + #{c' < c : n_c' > r},
+// A(r) = sum over r' < r of #{c : n_c > r'}.  Any 32 consecutive points then belong to
+// (almost always) 32 different classes, so the spreading threads can take the piece
+// in order -- every thread the same number of points -- and a warp's 32 atomics of a
+// tap step still hit 32 different banks.
+constexpr int kSortSmem = kChunk * (4 + 4 + 4 + 1);     // ids, masks, prefix, classes
 __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ payload, const uint8_t* __restrict__ cls,
-                                                    const int4* __restrict__ work, const int* __restrict__ counters,
-                                                    uint32_t* __restrict__ class_off) {
-    __shared__ uint32_t s_ids[kChunk];
-    __shared__ uint8_t s_cls[kChunk];
-    __shared__ int s_hist[32], s_cur[32];
+                                                    const int4* __restrict__ work, const int* __restrict__ counters) {
+    extern __shared__ uint32_t sm_u[];
+    uint32_t* s_ids = sm_u;                                     // kChunk
+    uint32_t* s_mask = s_ids + kChunk;                          // kChunk: classes with n_c > r
+    int* s_pre = reinterpret_cast<int*>(s_mask + kChunk);       // kChunk: A(r)
+    uint8_t* s_cls = reinterpret_cast<uint8_t*>(s_pre + kChunk);
+    __shared__ int s_hist[32], s_cur[32], s_off[32], s_maxn;
+    __shared__ int s_part[256];
     const int n_work = counters[0];
     for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
         const int4 wk = work[item];
+        const int len = wk.z;
         if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < wk.z; i += blockDim.x) {
-            const uint32_t id = payload[wk.y + i];
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
             const uint8_t c = cls[wk.y + i];
-            s_ids[i] = id;
+            s_ids[i] = payload[wk.y + i];
             s_cls[i] = c;
             atomicAdd(&s_hist[c], 1);
         }
         __syncthreads();
         if (threadIdx.x < 32) {
             const int h = s_hist[threadIdx.x];
-            int v = h;
+            int v = h, mx = h;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int u = __shfl_up_sync(0xffffffffu, v, o);
                 if ((int)threadIdx.x >= o) v += u;
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             }
+            s_off[threadIdx.x] = v - h;
             s_cur[threadIdx.x] = v - h;
-            class_off[(size_t)item * 32 + threadIdx.x] = (uint32_t)(v - h);
+            if (threadIdx.x == 0) s_maxn = mx;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < wk.z; i += blockDim.x) {
-            const int slot = atomicAdd(&s_cur[s_cls[i]], 1);
-            payload[wk.y + slot] = s_ids[i];
+        const int maxn = s_maxn;
+        // masks and per-thread partial sums of their popcounts (contiguous r ranges)
+        const int per = (maxn + blockDim.x - 1) / blockDim.x;
+        const int r0 = threadIdx.x * per, r1 = min(maxn, r0 + per);
+        int part = 0;
+        for (int r = r0; r < r1; ++r) {
+            uint32_t m = 0;
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) m |= (uint32_t)(s_hist[c] > r) << c;
+            s_mask[r] = m;
+            part += __popc(m);
+        }
+        s_part[threadIdx.x] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int i = 0; i < (int)blockDim.x; ++i) { const int t = s_part[i]; s_part[i] = acc; acc += t; }
+        }
+        __syncthreads();
+        int acc = s_part[threadIdx.x];
+        for (int r = r0; r < r1; ++r) { s_pre[r] = acc; acc += __popc(s_mask[r]); }
+        __syncthreads();
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            const int c = s_cls[i];
+            const int r = atomicAdd(&s_cur[c], 1) - s_off[c];
+            const int pos = s_pre[r] + __popc(s_mask[r] & ((1u << c) - 1u));
+            payload[wk.y + pos] = s_ids[i];
         }
         __syncthreads();
     }
@@ -288,7 +322,8 @@ static void bin_w(Plan& P, const BinArgs& a0, int nbricks) {
     k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work);
     a.count = w.cursor;
     k_bin<W, true><<<grid, 256, 0, P.stream>>>(a, M);
-    k_class_sort<<<P.num_sms * 5, 256, 0, P.stream>>>(w.payload, w.cls, w.work, w.counters, w.class_off);
+    cudaFuncSetAttribute(k_class_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+    k_class_sort<<<P.num_sms * 2, 256, kSortSmem, P.stream>>>(w.payload, w.cls, w.work, w.counters);
 }
 
 cudaError_t launch_bin(Plan& P, int M, bool kc) {
@@ -337,7 +372,6 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
 // ---------------------------------------------------------------------------
 struct SpreadArgs {
     const uint32_t* payload;
-    const uint32_t* class_off;   // per work item: offset of each bank class in the piece
     const int4* work;
     int* counters;
     const ImgGeom* geom;
@@ -373,7 +407,6 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
     float* lev2 = reinterpret_cast<float*>(sm_i + NC * RG3);   // NC * RG3 float
     __shared__ int s_item;
     __shared__ float s_red[kSpreadWarps];
-    __shared__ int s_redi[kSpreadWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_work = a.counters[0];
     for (;;) {
@@ -389,31 +422,26 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
         const int b = wk.x;
         const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
         const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * kBrick;
-        // this lane's bank class inside the piece, this warp's share of it
-        const uint32_t s0 = (uint32_t)wk.y + __ldg(&a.class_off[(size_t)item * 32 + lane]);
-        const uint32_t s1 = (uint32_t)wk.y + (lane < 31 ? __ldg(&a.class_off[(size_t)item * 32 + lane + 1]) : (uint32_t)wk.z);
-        const int my_n = (int)(s1 - s0) > warp ? (int)((s1 - s0 - warp + kSpreadWarps - 1) / kSpreadWarps) : 0;
-        // scale from the largest weight of the item, rounds from the longest share
+        // the piece is ordered round-robin over bank classes: thread i takes points
+        // i, i + 256, ... (every thread the same count, up to one)
+        const uint32_t s0 = (uint32_t)wk.y + threadIdx.x;
+        const int my_n = wk.z > (int)threadIdx.x ? (wk.z - (int)threadIdx.x + kSpreadThreads - 1) / kSpreadThreads : 0;
         float wmax = a.wmax_fixed;
         if (wmax <= 0.0f) {
             for (int i = 0; i < my_n; ++i) {
-                const uint32_t id = __ldg(&a.payload[s0 + warp + kSpreadWarps * i]);
+                const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
                 const float2 wv = point_weight(a, CPLX, (int)(id >> kTBits), (int)(id & ((1u << kTBits) - 1u)));
                 wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
             }
-        }
-        int rounds = (my_n + 1) / 2;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-            rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
-        }
-        if (lane == 0) { s_red[warp] = wmax; s_redi[warp] = rounds; }
-        __syncthreads();
-        wmax = s_red[0];
-        rounds = s_redi[0];
+            for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+            if (lane == 0) s_red[warp] = wmax;
+            __syncthreads();
+            wmax = s_red[0];
 #pragma unroll
-        for (int i = 1; i < kSpreadWarps; ++i) { wmax = fmaxf(wmax, s_red[i]); rounds = max(rounds, s_redi[i]); }
+            for (int i = 1; i < kSpreadWarps; ++i) wmax = fmaxf(wmax, s_red[i]);
+        }
+        const int rounds = (((wk.z + kSpreadThreads - 1) / kSpreadThreads) + 1) / 2;
         int ex = 0;
         if (wmax > 0.0f) frexpf(wmax, &ex);                // wmax <= 2^ex
         const float S = ldexpf(1.0f, 21 - ex), invS = ldexpf(1.0f, ex - 21);
@@ -422,7 +450,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
             for (int q = 0; q < 2; ++q) {
                 const int i = 2 * r + q;
                 if (i >= my_n) continue;
-                const uint32_t id = __ldg(&a.payload[s0 + warp + kSpreadWarps * i]);
+                const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
                 const int m = (int)(id >> kTBits);
                 const int t = (int)(id & ((1u << kTBits) - 1u));
                 const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
@@ -511,7 +539,6 @@ cudaError_t launch_spread(Plan& P, int M, bool kc) {
     if (e != cudaSuccess || M <= 0) return e;
     SpreadArgs a;
     a.payload = w.payload;
-    a.class_off = w.class_off;
     a.work = w.work;
     a.counters = w.counters;
     a.geom = w.geom;

@@ -141,9 +141,10 @@ def test_toeplitz_apply_matches_oracle(F):
 @pytest.mark.parametrize("W,tol", [(7, 1e-4), (6, 2e-4)])
 def test_cg_config1_matches_oracle(F, W, tol):
     """FIRM on the N=32 workload: 200 noiseless Haar views, no CTF, lam=0, 10 CG iterations;
-    the volume vs the oracle's after the same count.  Gate 1e-4 at W=7; at W=6 the window's
-    own 8e-6 error in Ker and A*b is amplified by the unregularised iteration (see the
-    precision notes), and the bound is 2e-4."""
+    the volume vs the oracle's after the same count.  Gate 1e-4 at W=7.  At W=6 the
+    window's own ~5e-6 error in A*b is amplified about 21x by the unregularised
+    iteration (test_c1_volume_sensitivity_to_rhs_perturbation measures this on the
+    oracle alone), so the gate is 2e-4."""
     inp = synth.config_inputs("C1")
     N, M = inp["N"], inp["M"]
     K, h = _oracle_h(inp)
@@ -211,8 +212,9 @@ def test_bad_arguments_are_rejected(F):
 
 
 def test_repeated_calls_agree(F):
-    """Same inputs, same plan, three calls: Ker, A*b and the CG iterate agree to FP32
-    rounding (the only run-to-run freedom is the order of FP32/FP64 additions)."""
+    """Same inputs, same plan, three calls: Ker and A*b agree to FP32 rounding (the only
+    run-to-run freedom is the order of the FP64 grid additions); CG on the same Ker and
+    A*b is bit-identical from call to call (its reductions have a fixed order)."""
     inp = synth.config_inputs("C1")
     N, M = inp["N"], inp["M"]
     rec = F.Reconstructor(N, M, W=7, lam=0.0)
@@ -227,14 +229,20 @@ def test_repeated_calls_agree(F):
         rhs = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
         rec.copy_out(F._lib.FIRM_OUT_KER, ker)
         rec.copy_out(F._lib.FIRM_OUT_RHS, rhs)
-        x = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
-        rec.cg_solve(x, 10)
         torch.cuda.synchronize()
-        outs.append((ker.cpu().numpy(), rhs.cpu().numpy(), x.cpu().numpy()))
-    for name, i in (("Ker", 0), ("A*b", 1), ("x10", 2)):
+        outs.append((ker.cpu().numpy(), rhs.cpu().numpy()))
+    for name, i in (("Ker", 0), ("A*b", 1)):
         d = max(rel(o[i], outs[0][i]) for o in outs[1:])
         print(f"repeat {name}: max rel diff {d:.3e}")
-        assert d <= (1e-6 if i < 2 else 2e-5), (name, d)
+        assert d <= 1e-6, (name, d)
+    xs = []
+    for _ in range(3):
+        x = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+        st, it = rec.cg_solve(x, 10)
+        assert st == 0 and it == 10
+        xs.append(x.cpu().numpy())
+    for x in xs[1:]:
+        assert np.array_equal(x, xs[0])
 
 
 def test_preconditioned_cg_matches_oracle(F):
@@ -266,9 +274,10 @@ def test_preconditioned_cg_matches_oracle(F):
     st, it_pc = rec.cg_solve(x, 500, rel_tol=1e-4)
     rec.set_precond(F._lib.FIRM_PRECOND_NONE)
     x2 = torch.empty_like(x)
-    st2, it_plain = rec.cg_solve(x2, 500, rel_tol=1e-4)
+    # plain CG needs several hundred iterations here; if it hits the cap, the cap is its count
+    st2, it_plain = rec.cg_solve(x2, 2000, rel_tol=1e-4, allow=(F._lib.FIRM_ENOTCONV,))
     torch.cuda.synchronize()
-    print(f"iterations to rel-res 1e-4: plain {it_plain}, circulant {it_pc}")
-    assert st == 0 and st2 == 0 and it_pc < it_plain
+    print(f"iterations to rel-res 1e-4: plain {it_plain} (status {st2}), circulant {it_pc}")
+    assert st == 0 and it_pc < it_plain
     true_res = np.linalg.norm(op(x.cpu().numpy().astype(np.float64)) - rhs) / np.linalg.norm(rhs)
     assert true_res <= 3e-4

@@ -480,3 +480,29 @@ def test_features_sum_to_one_and_identity_rotation_lies_in_cone_zero():
     ref = np.zeros(64)
     np.add.at(ref, shell, (h * h).sum(0))
     np.testing.assert_allclose(f[:, 0], ref / ref.sum(), rtol=1e-12)
+
+
+# -- sensitivity of the 10-iteration, lambda = 0 volume ------------------------
+
+def test_c1_volume_sensitivity_to_rhs_perturbation():
+    """Section 3.3 CG, N=32 workload (200 Haar views, lambda = 0, 10 iterations): a white
+    perturbation of A*b of relative L2 size 1e-5 moves the oracle's own 10-iteration
+    volume by about 2e-4 (about 21x).  This fixes how far any path whose A*b is within
+    1e-5 of the exact one (a W=6, sigma=2 window is at ~5e-6) can land from the oracle
+    volume, and is the basis of the W=6 volume gate of the GPU parity test."""
+    inp = synth.config_inputs("C1")
+    N = inp["N"]
+    K = O.disc(N)
+    h = np.ones((inp["M"], K.shape[0]))
+    Ker = O.kernel(inp["R"], h, K, N).real
+    rhs = O.backproject(inp["images"].astype(np.float64), inp["shifts"], inp["R"], h, K)
+    Kh = O.khat(Ker).real
+    op = lambda v: O.toeplitz_apply(Kh, v).real
+    x0, _, _ = O.cg(op, rhs, 10)
+    amp = []
+    for seed in (0, 1):
+        g = np.random.default_rng(seed).standard_normal(rhs.shape)
+        g *= 1e-5 * np.linalg.norm(rhs) / np.linalg.norm(g)
+        x1, _, _ = O.cg(op, rhs + g, 10)
+        amp.append(np.linalg.norm(x1 - x0) / np.linalg.norm(x0) / 1e-5)
+    assert 10 <= min(amp) and max(amp) <= 40, amp
