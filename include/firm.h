@@ -74,7 +74,7 @@ typedef struct {
 } firm_ctf_group;
 
 typedef struct {
-    int N;            /* volume edge: 16, 32, 48, 64, 96 or 128 */
+    int N;            /* volume edge: 16, 32, 48, 64, 80, 96 or 128 */
     int M;            /* largest image count any call on the plan will pass */
     int n_groups;     /* defocus groups in the CTF table; 0 means no CTF (h = 1) */
     int W;            /* Kaiser-Bessel window width in fine-grid cells: 6, 7 or 8 */
@@ -239,6 +239,63 @@ int firm_launch_count(firm_plan_t plan, long long* out);
 
 void firm_destroy(firm_plan_t plan);
 const char* firm_strerror(int code);
+
+/* ---- Batched reconstructions ------------------------------------------------------
+ * Many independent FIRM reconstructions (Section 3.4, steps 1-4 each: Ker, A*b, K-hat,
+ * then a fixed number of CG iterations from x0 = 0) run as one unit of work.  Each
+ * reconstruction is a plan of its own (its own N, image count, CTF table and
+ * workspace); all plans of a batch share W and the device.  The paper reconstructs
+ * one volume at a time: batching is an execution form of the same steps, and each
+ * volume equals what firm_kernel + firm_backproject + firm_cg_solve(max_iter = iters,
+ * rel_tol = 0) give for that plan, up to the order of floating-point additions.
+ *
+ * Execution: the plans' stages are queued on n_streams worker streams forked from
+ * the batch's stream (plans dealt out largest first).  With FIRM_BATCH_PERSISTENT the
+ * spreading of every plan (each channel) is one persistent launch over one shared
+ * queue of work items; otherwise each plan spreads on its own stream.  With
+ * FIRM_BATCH_GRAPH the whole batch is captured once into a CUDA graph and replayed
+ * while the items, iteration count, flags and tuning stay the same (changing any of
+ * them captures a new graph).
+ *
+ * The batch needs a small device workspace from the caller (descriptors and work
+ * queues): firm_batch_workspace_size.  It creates its own CUDA streams and events. */
+typedef struct firm_batch_s* firm_batch_t;
+
+typedef struct {
+    int M;                  /* images of this reconstruction, 0 <= M <= the plan's M */
+    const double* R;        /* device, M x 9 float64 */
+    const int32_t* group;   /* device, M int32, or NULL (every image in group 0) */
+    const void* images;     /* device, M x N x N in the plan's image dtype */
+    const double* shifts;   /* device, M x 2 float64, or NULL (no shifts) */
+    float* x;               /* device, N^3 float32: the reconstructed volume */
+} firm_batch_item;
+
+enum { FIRM_BATCH_GRAPH = 1, FIRM_BATCH_PERSISTENT = 2 };
+
+int firm_batch_workspace_size(int n_plans, size_t* bytes);
+/* plans: n_plans distinct plans (not destroyed while the batch lives).  n_streams in
+ * 1..64 (worker streams; the tuner may lower it).  stream: the batch's cudaStream_t;
+ * plans' own streams are not used by batch runs. */
+int firm_batch_create(firm_batch_t* out, int n_plans, const firm_plan_t* plans, int n_streams, void* workspace,
+                      size_t workspace_bytes, void* stream);
+/* Queues every reconstruction (items[i] for plans[i]) on the batch's stream and
+ * returns without waiting.  iters in 0..20000; flags: FIRM_BATCH_*. */
+int firm_batch_run(firm_batch_t batch, const firm_batch_item* items, int iters, int flags);
+/* Waits for the batch, then reports per plan the CG status (firm_status) and the
+ * iterations run; also leaves each plan as after its own firm_kernel /
+ * firm_backproject (lam_eff, Ker, K-hat and A*b readable).  Returns FIRM_OK when every
+ * plan is OK, else the first failing status.  status, iters: n_plans entries or NULL. */
+int firm_batch_wait(firm_batch_t batch, int* status, int* iters);
+/* Tuning knobs: active worker streams (1..n_streams of create) and the points per
+ * spreading work item of every plan (1024..8192, a multiple of 256).  firm_batch_tune
+ * times the candidates on the given items (each candidate run twice, the second
+ * timed with CUDA events) and keeps the fastest; ms_out (nullable) gets its time. */
+int firm_batch_set_config(firm_batch_t batch, int n_streams, int chunk);
+int firm_batch_get_config(firm_batch_t batch, int* n_streams, int* chunk);
+int firm_batch_tune(firm_batch_t batch, const firm_batch_item* items, int iters, int flags, double* ms_out);
+/* Kernels one run of the batch launches (graph or not), counted when queued. */
+int firm_batch_launch_count(firm_batch_t batch, long long* out);
+void firm_batch_destroy(firm_batch_t batch);
 
 #ifdef __cplusplus
 }

@@ -36,7 +36,7 @@ __all__ = [
     "forward", "adjoint", "kernel", "kernel_at", "adjoint_at", "image_dft",
     "backproject", "backproject_at", "circulant_column", "khat", "khat_half",
     "toeplitz_direct", "toeplitz_apply", "lambda_eff", "cg", "wrapped_spectrum",
-    "circulant_preconditioner",
+    "circulant_preconditioner", "sums_at_voxels",
 ]
 
 
@@ -184,6 +184,26 @@ def _at_voxels(R, H, K, N, nvox, chunk=512):
         T = np.matmul(Ea, Hs)                                              # (m, v, k2)
         out += np.einsum("mvj,mvj->v", T, Eb)
     return out
+
+
+def sums_at_voxels(R, group_id, h_groups, images, shifts, K, N, nvox):
+    """Ker(n) and A*b(n) (eq. kernel, eq. backprojection) at the voxels nvox, summed over
+    the images given (a slice of a large set: the caller adds the slices).  The weights
+    are built per chunk of images from the per-group table h_groups (G, |K|) instead of
+    an (M, |K|) array.  Also returns the l1 norms of the weights, sum h^2 and sum |h b|,
+    which bound the size of every output value."""
+    ker = np.zeros(len(nvox), complex)
+    rhs = np.zeros(len(nvox), complex)
+    l1k = l1r = 0.0
+    for a in range(0, R.shape[0], 1024):
+        b = min(R.shape[0], a + 1024)
+        h = h_groups[group_id[a:b]]
+        g = image_dft(images[a:b].astype(np.float64), K, shifts[a:b]) * h
+        ker += _at_voxels(R[a:b], h * h, K, N, nvox)
+        rhs += _at_voxels(R[a:b], g, K, N, nvox)
+        l1k += float((h * h).sum())
+        l1r += float(np.abs(g).sum())
+    return ker, rhs, l1k, l1r
 
 
 def kernel_at(R, h, K, N, nvox):

@@ -14,3 +14,4 @@ from ._lib import (  # noqa: F401
     firm_toeplitz_apply, firm_workspace_size, make_groups, make_params,
 )
 from .recon import Reconstructor  # noqa: F401
+from .batch import BatchReconstructor  # noqa: F401

@@ -19,13 +19,17 @@ FIRM_IMG_F32, FIRM_IMG_BF16 = 0, 1
 FIRM_LAMBDA_RELATIVE, FIRM_LAMBDA_ABSOLUTE = 0, 1
 FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES = 0, 1, 2, 3
 FIRM_PRECOND_NONE, FIRM_PRECOND_CIRCULANT, FIRM_PRECOND_BINNED, FIRM_PRECOND_TABLE = 0, 1, 2, 3
+FIRM_BATCH_GRAPH, FIRM_BATCH_PERSISTENT = 1, 2
 
 EXPORTED = [
     "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_cg_solve",
     "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_set_precond", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
     "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_target", "firm_pc_axis",
     "firm_set_precond_table", "firm_mlp_forward", "firm_mlp_to_bf16", "firm_mlp_forward_bf16", "firm_mlp_grad",
-    "firm_mlp_adam", "firm_mlp_param_count", "firm_mlp_work_floats", "firm_destroy", "firm_strerror",
+    "firm_mlp_adam", "firm_mlp_param_count", "firm_mlp_work_floats",
+    "firm_batch_workspace_size", "firm_batch_create", "firm_batch_run", "firm_batch_wait", "firm_batch_set_config",
+    "firm_batch_get_config", "firm_batch_tune", "firm_batch_launch_count", "firm_batch_destroy",
+    "firm_destroy", "firm_strerror",
 ]
 
 
@@ -39,6 +43,11 @@ class firm_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("n_groups", ctypes.c_int), ("W", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("lambda_", ctypes.c_double), ("lambda_mode", ctypes.c_int),
                 ("disc_mode", ctypes.c_int), ("img_dtype", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class firm_batch_item(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("R", ctypes.c_void_p), ("group", ctypes.c_void_p), ("images", ctypes.c_void_p),
+                ("shifts", ctypes.c_void_p), ("x", ctypes.c_void_p)]
 
 
 class FirmError(RuntimeError):
@@ -83,12 +92,22 @@ def lib() -> ctypes.CDLL:
     L.firm_mlp_param_count.argtypes = []
     L.firm_mlp_work_floats.argtypes = [i]
     L.firm_mlp_work_floats.restype = ctypes.c_size_t
+    L.firm_batch_workspace_size.argtypes = [i, ctypes.POINTER(ctypes.c_size_t)]
+    L.firm_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), i, vp, ctypes.c_size_t, vp]
+    L.firm_batch_run.argtypes = [vp, ctypes.POINTER(firm_batch_item), i, i]
+    L.firm_batch_wait.argtypes = [vp, vp, vp]
+    L.firm_batch_set_config.argtypes = [vp, i, i]
+    L.firm_batch_get_config.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.firm_batch_tune.argtypes = [vp, ctypes.POINTER(firm_batch_item), i, i, ctypes.POINTER(d)]
+    L.firm_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.firm_batch_destroy.argtypes = [vp]
+    L.firm_batch_destroy.restype = None
     L.firm_destroy.argtypes = [vp]
     L.firm_destroy.restype = None
     L.firm_strerror.argtypes = [i]
     L.firm_strerror.restype = ctypes.c_char_p
     for name in EXPORTED[:-2]:
-        if name != "firm_mlp_work_floats":
+        if name not in ("firm_mlp_work_floats", "firm_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -265,3 +284,69 @@ def firm_mlp_adam(params, grad, m, v, step, lr, stream=0):
 def firm_destroy(plan):
     if plan:
         lib().firm_destroy(plan)
+
+
+# ---- batched reconstructions ----
+
+def make_batch_items(items) -> ctypes.Array:
+    """items: sequence of dicts with M, R, group, images, shifts, x (device tensors or None)."""
+    arr = (firm_batch_item * len(items))()
+    for k, it in enumerate(items):
+        arr[k] = firm_batch_item(int(it["M"]), _ptr(it["R"]), _ptr(it.get("group")), _ptr(it["images"]),
+                                 _ptr(it.get("shifts")), _ptr(it["x"]))
+    return arr
+
+
+def firm_batch_workspace_size(n_plans: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().firm_batch_workspace_size(int(n_plans), ctypes.byref(n)), "firm_batch_workspace_size")
+    return int(n.value)
+
+
+def firm_batch_create(plans, n_streams: int, workspace, workspace_bytes: int, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(plans))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    _check(lib().firm_batch_create(ctypes.byref(h), len(plans), arr, int(n_streams), _ptr(workspace),
+                                   int(workspace_bytes), stream), "firm_batch_create")
+    return h
+
+
+def firm_batch_run(batch, items_arr, iters: int, flags: int):
+    _check(lib().firm_batch_run(batch, items_arr, int(iters), int(flags)), "firm_batch_run")
+
+
+def firm_batch_wait(batch, n: int, allow=()):
+    """Returns (status, per-plan statuses, per-plan iterations)."""
+    st = np.zeros(n, np.int32)
+    it = np.zeros(n, np.int32)
+    r = lib().firm_batch_wait(batch, st.ctypes.data, it.ctypes.data)
+    if r != FIRM_OK and r not in allow:
+        raise FirmError(r, "firm_batch_wait")
+    return r, st, it
+
+
+def firm_batch_set_config(batch, n_streams: int, chunk: int):
+    _check(lib().firm_batch_set_config(batch, int(n_streams), int(chunk)), "firm_batch_set_config")
+
+
+def firm_batch_get_config(batch):
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().firm_batch_get_config(batch, ctypes.byref(a), ctypes.byref(b)), "firm_batch_get_config")
+    return int(a.value), int(b.value)
+
+
+def firm_batch_tune(batch, items_arr, iters: int, flags: int) -> float:
+    ms = ctypes.c_double(0)
+    _check(lib().firm_batch_tune(batch, items_arr, int(iters), int(flags), ctypes.byref(ms)), "firm_batch_tune")
+    return float(ms.value)
+
+
+def firm_batch_launch_count(batch) -> int:
+    v = ctypes.c_longlong(0)
+    _check(lib().firm_batch_launch_count(batch, ctypes.byref(v)), "firm_batch_launch_count")
+    return int(v.value)
+
+
+def firm_batch_destroy(batch):
+    if batch:
+        lib().firm_batch_destroy(batch)

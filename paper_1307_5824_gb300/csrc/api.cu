@@ -148,7 +148,7 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     const size_t Gk = 4 * N, Gr = 2 * N;
     const size_t nbk = Gk / kBrick;
     const size_t nb3 = nbk * nbk * nbk;
-    const size_t max_work = nb3 + M * nH / kChunk + 2;
+    const size_t max_work = nb3 + M * nH / kMinChunk + 2;
     const size_t esz = p.img_dtype == FIRM_IMG_BF16 ? 2 : 4;
     const size_t N3 = N * N * N, H3 = 2 * N * 2 * N * (N + 1);
     Carver c{base};
@@ -186,7 +186,7 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.khat = c.take<float>(H3);
     w.rhs = c.take<float>(N3);
     w.x = c.take<float>(N3);
-    w.r = c.take<double>(N3);
+    w.r = c.take<float2>(N3);
     w.p = c.take<float>(N3);
     w.q = c.take<float>(N3);
     w.t1 = c.take<float2>(N * N * (N + 1));
@@ -201,12 +201,13 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.red_b = c.take<double>(kRedSlots);
     w.hist = c.take<double>(kMaxHist);
     w.cg = c.take<CgState>(1);
+    w.lam = c.take<float>(2);
     w.total = c.off + 256;
     return w.total;
 }
 
 static bool supported_N(int N) {
-    return N == 16 || N == 32 || N == 48 || N == 64 || N == 96 || N == 128;
+    return N == 16 || N == 32 || N == 48 || N == 64 || N == 80 || N == 96 || N == 128;
 }
 
 static int check_params(const firm_params* p) {
@@ -344,10 +345,6 @@ static int build_preconditioner(Plan& P) {
 
 using namespace firm;
 
-struct firm_plan_s {
-    Plan P;
-};
-
 extern "C" {
 
 int firm_workspace_size(const firm_params* p, size_t* bytes) {
@@ -387,7 +384,7 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
     P.nK = disc_size(p->N);
     P.nH = (P.nK + 1) / 2;
     P.n_ctf = p->n_groups > 0 ? p->n_groups : 1;
-    P.max_work = (size_t)P.nbk * P.nbk * P.nbk + (size_t)p->M * P.nH / kChunk + 2;
+    P.max_work = (size_t)P.nbk * P.nbk * P.nbk + (size_t)p->M * P.nH / kMinChunk + 2;
     for (int g = 0; g < p->n_groups; ++g) P.groups.push_back(groups[g]);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -481,11 +478,11 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     tm.stop();
     tm.start(3);
     FIRM_CK(launch_khat(P));
+    FIRM_CK(launch_lam_eff(P));
     tm.stop();
-    // lam_eff from Ker(0) (the n = 0 entry of the half box)
+    // lam_eff from Ker(0) (the n = 0 entry of the half box), also kept on the host
     float ker0 = 0.f;
-    const size_t i0 = ((size_t)P.N * 2 * P.N + P.N) * (P.N + 1);
-    FIRM_CK(cudaMemcpyAsync(&ker0, w.ker + i0, sizeof(float), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaMemcpyAsync(&ker0, w.lam + 1, sizeof(float), cudaMemcpyDeviceToHost, P.stream));
     int st = check_spread_flag(P);
     if (st != FIRM_OK) return st;
     P.lam_eff = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda * (double)ker0 : P.p.lambda;
@@ -550,7 +547,7 @@ int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y) {
     const bool ydev = is_device(y);
     float* yd = ydev ? y : w.q;
     if (xd == yd) return FIRM_EINVAL;
-    FIRM_CK(launch_toeplitz(P, xd, yd, (float)P.lam_eff, nullptr, nullptr));
+    FIRM_CK(launch_toeplitz(P, xd, yd, nullptr, nullptr));
     if (!ydev) return put_out(y, yd, n * sizeof(float), P.stream);
     return FIRM_OK;
 }
@@ -578,7 +575,7 @@ int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, do
     if (use_pc) FIRM_CK(launch_precond(P, w.r, w.z, w.cg));
     const int batch = 8;
     for (int it = 0; it < max_iter; ++it) {
-        FIRM_CK(launch_toeplitz(P, w.p, w.q, (float)P.lam_eff, w.r, w.cg, use_pc ? w.z : nullptr));
+        FIRM_CK(launch_toeplitz(P, w.p, w.q, w.r, w.cg, use_pc ? w.z : nullptr));
         FIRM_CK(launch_cg_update(P));
         if (use_pc) FIRM_CK(launch_precond(P, w.r, w.z, w.cg));
         if (rel_tol > 0.0 && ((it + 1) % batch == 0) && it + 1 < max_iter) {

@@ -7,18 +7,20 @@
 // to finish (ticket counter) sums the partials in block order.  All scalar logic
 // (alpha, beta, the stop test, breakdown) runs on the device; a kernel that finds
 // the `done` flag set returns at once, so batches of iterations can be queued
-// without reading anything back.
+// without reading anything back.  Scalars are FP64; the residual vector and the
+// per-thread parts of the inner products are double-words (dw.cuh), so no kernel
+// does FP64 arithmetic per element.
 #include <cuda_runtime.h>
 
+#include "dw.cuh"
 #include "firm_internal.h"
 
 namespace firm {
 
 constexpr int kCgThreads = 256;
 
-__device__ __forceinline__ double block_sum(double v, double* s_warp) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+__device__ __forceinline__ double block_sum(float2 v2, double* s_warp) {
+    const double v = dw_to_double(dw_warp_sum(v2));
     if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
     __syncthreads();
     double b = 0.0;
@@ -54,19 +56,19 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket, bool* s_last) {
 }
 
 __global__ void __launch_bounds__(kCgThreads) k_cg_init(const float* __restrict__ rhs, float* __restrict__ x,
-                                                        double* __restrict__ r, float* __restrict__ p, size_t n,
+                                                        float2* __restrict__ r, float* __restrict__ p, size_t n,
                                                         CgState* cg, double* red, double* hist, int max_iter,
                                                         double rel_tol, int use_pc) {
     __shared__ double s_warp[kCgThreads / 32];
     __shared__ double s_fin[kCgThreads];
     __shared__ bool s_last;
-    double acc = 0.0;
+    float2 acc = make_float2(0.0f, 0.0f);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float b = rhs[i];
         x[i] = 0.0f;
-        r[i] = (double)b;
+        r[i] = make_float2(b, 0.0f);
         p[i] = b;
-        acc += (double)b * (double)b;
+        acc = dw_acc_prod(acc, b, b);
     }
     const double bs = block_sum(acc, s_warp);
     if (threadIdx.x == 0) red[blockIdx.x] = bs;
@@ -76,6 +78,9 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(const float* __restrict_
         cg->rr = rr;
         cg->pq = 0.0;
         cg->beta = 0.0;
+        cg->beta_f[0] = cg->beta_f[1] = 0.0f;
+        cg->alpha = 0.0;
+        cg->alpha_f[0] = cg->alpha_f[1] = 0.0f;
         cg->bnorm = sqrt(rr);
         cg->tol = rel_tol > 0.0 ? rel_tol * sqrt(rr) : 0.0;
         cg->it = 0;
@@ -91,7 +96,9 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(const float* __restrict_
     }
 }
 
-__global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x, double* __restrict__ r,
+// x += alpha p, r -= alpha q (alpha from the Toeplitz apply's last block), then
+// <r, r> and the next beta.
+__global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x, float2* __restrict__ r,
                                                           const float* __restrict__ p, const float* __restrict__ q,
                                                           size_t n4, CgState* cg, double* red, double* hist) {
     __shared__ double s_warp[kCgThreads / 32];
@@ -99,27 +106,31 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x,
     __shared__ bool s_last;
     if (cg->done) return;
     const double pq = cg->pq, rr = cg->rr;
-    const double alpha = (cg->use_pc ? cg->rz : rr) / pq;
-    const bool ok = pq > 0.0 && isfinite(alpha);
-    double acc = 0.0;
+    const bool ok = pq > 0.0 && isfinite(cg->alpha);
+    float2 acc = make_float2(0.0f, 0.0f);
     if (ok) {
-        const float a = (float)alpha;
+        const float2 a = make_float2(cg->alpha_f[0], cg->alpha_f[1]);
         float4* x4 = reinterpret_cast<float4*>(x);
-        double2* r2 = reinterpret_cast<double2*>(r);
+        float4* r4 = reinterpret_cast<float4*>(r);
         const float4* p4 = reinterpret_cast<const float4*>(p);
         const float4* q4 = reinterpret_cast<const float4*>(q);
         for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
             float4 xv = x4[i];
             const float4 pv = p4[i], qv = q4[i];
-            double2 ra = r2[2 * i], rb = r2[2 * i + 1];
-            xv.x = fmaf(a, pv.x, xv.x); xv.y = fmaf(a, pv.y, xv.y);
-            xv.z = fmaf(a, pv.z, xv.z); xv.w = fmaf(a, pv.w, xv.w);
-            ra.x = fma(-alpha, (double)qv.x, ra.x); ra.y = fma(-alpha, (double)qv.y, ra.y);
-            rb.x = fma(-alpha, (double)qv.z, rb.x); rb.y = fma(-alpha, (double)qv.w, rb.y);
+            const float4 ra = r4[2 * i], rb = r4[2 * i + 1];      // (hi, lo) of 4 elements
+            xv.x = fmaf(a.x, pv.x, xv.x); xv.y = fmaf(a.x, pv.y, xv.y);
+            xv.z = fmaf(a.x, pv.z, xv.z); xv.w = fmaf(a.x, pv.w, xv.w);
+            const float2 r0 = dw_sub_mul(make_float2(ra.x, ra.y), a, qv.x);
+            const float2 r1 = dw_sub_mul(make_float2(ra.z, ra.w), a, qv.y);
+            const float2 r2 = dw_sub_mul(make_float2(rb.x, rb.y), a, qv.z);
+            const float2 r3 = dw_sub_mul(make_float2(rb.z, rb.w), a, qv.w);
             x4[i] = xv;
-            r2[2 * i] = ra;
-            r2[2 * i + 1] = rb;
-            acc += ra.x * ra.x + ra.y * ra.y + rb.x * rb.x + rb.y * rb.y;
+            r4[2 * i] = make_float4(r0.x, r0.y, r1.x, r1.y);
+            r4[2 * i + 1] = make_float4(r2.x, r2.y, r3.x, r3.y);
+            acc = dw_acc_sq(acc, r0);
+            acc = dw_acc_sq(acc, r1);
+            acc = dw_acc_sq(acc, r2);
+            acc = dw_acc_sq(acc, r3);
         }
     }
     const double bs = block_sum(acc, s_warp);
@@ -135,7 +146,13 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x,
             const int it = cg->it + 1;
             cg->it = it;
             hist[it < kMaxHist ? it : kMaxHist - 1] = sqrt(rr_new);
-            if (!cg->use_pc) cg->beta = rr_new / rr;    // else set by the preconditioner pass
+            if (!cg->use_pc) {                        // else set by the preconditioner pass
+                const double beta = rr_new / rr;
+                cg->beta = beta;
+                const float2 bf = dw_from_double(beta);
+                cg->beta_f[0] = bf.x;
+                cg->beta_f[1] = bf.y;
+            }
             cg->rr = rr_new;
             if (cg->tol > 0.0 && sqrt(rr_new) <= cg->tol) cg->done = 1;
             if (it >= cg->max_iter) cg->done = 1;

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "dw.cuh"
 #include "fft.cuh"
 #include "firm_internal.h"
 
@@ -95,18 +96,20 @@ struct NoFinish {
     __device__ __forceinline__ void finish() const {}
 };
 
-// Transform lengths instantiated: 2N and 4N for N in {16, 32, 48, 64, 96, 128}.
+// Transform lengths instantiated: 2N and 4N for N in {16, 32, 48, 64, 80, 96, 128}.
 #define FIRM_CASE_L(V, ...) case V: { constexpr int LL = V; __VA_ARGS__; } break;
 #define FIRM_SWITCH_2N(Lval, ...)                                                             \
     switch (Lval) {                                                                          \
         FIRM_CASE_L(32, __VA_ARGS__) FIRM_CASE_L(64, __VA_ARGS__) FIRM_CASE_L(96, __VA_ARGS__)   \
-        FIRM_CASE_L(128, __VA_ARGS__) FIRM_CASE_L(192, __VA_ARGS__) FIRM_CASE_L(256, __VA_ARGS__) \
+        FIRM_CASE_L(128, __VA_ARGS__) FIRM_CASE_L(160, __VA_ARGS__) FIRM_CASE_L(192, __VA_ARGS__) \
+        FIRM_CASE_L(256, __VA_ARGS__)                                                          \
         default: return cudaErrorInvalidValue;                                               \
     }
 #define FIRM_SWITCH_4N(Lval, ...)                                                             \
     switch (Lval) {                                                                          \
         FIRM_CASE_L(64, __VA_ARGS__) FIRM_CASE_L(128, __VA_ARGS__) FIRM_CASE_L(192, __VA_ARGS__) \
-        FIRM_CASE_L(256, __VA_ARGS__) FIRM_CASE_L(384, __VA_ARGS__) FIRM_CASE_L(512, __VA_ARGS__) \
+        FIRM_CASE_L(256, __VA_ARGS__) FIRM_CASE_L(320, __VA_ARGS__) FIRM_CASE_L(384, __VA_ARGS__) \
+        FIRM_CASE_L(512, __VA_ARGS__)                                                          \
         default: return cudaErrorInvalidValue;                                               \
     }
 
@@ -209,6 +212,22 @@ cudaError_t launch_khat(Plan& P) {
     });
     P.launches += 3;
     return e;
+}
+
+// lam_eff = lambda Ker(0) (relative reading) or lambda (absolute), on the device, so that
+// the Toeplitz apply needs no host round trip; Ker(0) sits at (j3, j2, j1) = (N, N, 0).
+__global__ void k_lam_eff(const float* __restrict__ ker, size_t i0, double lambda, int relative, float* lam) {
+    const float k0 = ker[i0];
+    lam[0] = relative ? (float)(lambda * (double)k0) : (float)lambda;
+    lam[1] = k0;
+}
+
+cudaError_t launch_lam_eff(Plan& P) {
+    const size_t i0 = ((size_t)P.N * 2 * P.N + P.N) * (P.N + 1);
+    k_lam_eff<<<1, 1, 0, P.stream>>>(P.ws.ker, i0, P.p.lambda, P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? 1 : 0,
+                                     P.ws.lam);
+    P.launches += 1;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -343,6 +362,7 @@ cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* s
         case 32: return bf ? image_dft_n<32, uint16_t>(P, M, a) : image_dft_n<32, float>(P, M, a);
         case 48: return bf ? image_dft_n<48, uint16_t>(P, M, a) : image_dft_n<48, float>(P, M, a);
         case 64: return bf ? image_dft_n<64, uint16_t>(P, M, a) : image_dft_n<64, float>(P, M, a);
+        case 80: return bf ? image_dft_n<80, uint16_t>(P, M, a) : image_dft_n<80, float>(P, M, a);
         case 96: return bf ? image_dft_n<96, uint16_t>(P, M, a) : image_dft_n<96, float>(P, M, a);
         case 128: return bf ? image_dft_n<128, uint16_t>(P, M, a) : image_dft_n<128, float>(P, M, a);
         default: return cudaErrorInvalidValue;
@@ -353,13 +373,17 @@ cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* s
 // Toeplitz apply (CG-fused when cg != nullptr)
 // ---------------------------------------------------------------------------
 struct TRowsFwdOp : NoFinish {
-    const float* x; float* p; const double* r; const CgState* cg; float2* out; const float2* tw; int n_rows, N;
+    const float* x; float* p; const float2* r; const CgState* cg; float2* out; const float2* tw; int n_rows, N;
     const float* z = nullptr;   // preconditioned residual: p = z + beta p when set
     __device__ __forceinline__ float2 load(int row, int n) const {
         if (n >= N) return make_float2(0.0f, 0.0f);
         const size_t i = (size_t)row * N + n;
-        if (cg) {   // p = r + beta p (r FP64) or p = z + beta p, written back
-            const float v = (float)fma(cg->beta, (double)p[i], z ? (double)__ldg(&z[i]) : __ldg(&r[i]));
+        if (cg) {   // p = r + beta p (r, beta double-words) or p = z + beta p, written back
+            const float pv = p[i];
+            float bh, bl;
+            if (z) { bh = __ldg(&z[i]); bl = 0.0f; }
+            else { const float2 rv = __ldg(&r[i]); bh = rv.x; bl = rv.y; }
+            const float v = fmaf(cg->beta_f[0], pv, bh) + fmaf(cg->beta_f[1], pv, bl);
             p[i] = v;
             return make_float2(v, 0.0f);
         }
@@ -390,7 +414,8 @@ struct TColsYInvOp {
 struct TRowsInvOp {
     const float2* in; const float* x; float* y; double* red; CgState* cg; const float2* tw;
     int n_rows, N; float scale, lam;
-    double* acc;   // per-thread partial <x, y> (CG)
+    const float* lam_p;   // device lam_eff (overrides lam when set)
+    float2* acc;   // per-thread partial <x, y> (CG), double-word
     __device__ __forceinline__ float2 load(int row, int n) const {
         const float2* rr = in + (size_t)row * (N + 1);
         return n <= N ? __ldg(&rr[n]) : c_conj(__ldg(&rr[2 * N - n]));
@@ -399,9 +424,9 @@ struct TRowsInvOp {
         if (k >= N) return;
         const size_t i = (size_t)row * N + k;
         const float xv = __ldg(&x[i]);
-        const float yv = fmaf(v.x, scale, lam * xv);
+        const float yv = fmaf(v.x, scale, (lam_p ? __ldg(lam_p) : lam) * xv);
         y[i] = yv;
-        if (cg) *acc += (double)xv * (double)yv;
+        if (cg) *acc = dw_acc_prod(*acc, xv, yv);
     }
     __device__ __forceinline__ void finish() const {}
 };
@@ -435,16 +460,15 @@ __global__ void __launch_bounds__(kThreads) k_toep_rows_inv(TRowsInvOp op) {
     constexpr int ROWS = rows_per_block<L>();
     const int r0 = blockIdx.x * ROWS;
     const int nl = min(ROWS, op.n_rows - r0);
-    double acc = 0.0;
+    float2 acc = make_float2(0.0f, 0.0f);
     op.acc = &acc;
     auto ld = [&](int line, int n) { return op.load(r0 + line, n); };
     auto st = [&](int line, int k, float2 v) { op.store(r0 + line, k, v); };
     block_fft<L, +1, false>(nl, ld, st, S, op.tw);
     if (!op.cg) return;
     // block reduction
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    const float2 wsum = dw_warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = dw_to_double(wsum);
     __syncthreads();
     if (threadIdx.x == 0) {
         double b = 0.0;
@@ -469,7 +493,13 @@ __global__ void __launch_bounds__(kThreads) k_toep_rows_inv(TRowsInvOp op) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        op.cg->pq = s_fin[0];
+        const double pq = s_fin[0];
+        const double alpha = (op.cg->use_pc ? op.cg->rz : op.cg->rr) / pq;
+        op.cg->pq = pq;
+        op.cg->alpha = alpha;
+        const float2 af = dw_from_double(isfinite(alpha) ? alpha : 0.0);
+        op.cg->alpha_f[0] = af.x;
+        op.cg->alpha_f[1] = af.y;
         op.cg->ticket_a = 0;
     }
 }
@@ -500,7 +530,7 @@ __global__ void __launch_bounds__(kThreads) k_cols_cg(const Op op, const CgState
 }
 
 template <int L>
-static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg,
+static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, const float2* cg_r, CgState* cg,
                               const float* cg_z) {
     Workspace& w = P.ws;
     const int N = P.N;
@@ -530,7 +560,7 @@ static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, cons
     k_cols_cg<L, +1, TColsYInvOp><<<N * tiles_b, kThreads, smem_cols, P.stream>>>(d, cg);
     // pass 5: rows inverse (Hermitian), crop, scale, + lam x, <x, y>
     const float scale = 1.0f / ((float)L * (float)L * (float)L);
-    TRowsInvOp f{w.t1, x, y, w.red_a, cg, w.tw_2n, N * N, N, scale, lam, nullptr};
+    TRowsInvOp f{w.t1, x, y, w.red_a, cg, w.tw_2n, N * N, N, scale, 0.0f, w.lam, nullptr};
     if ((e = cudaFuncSetAttribute(k_toep_rows_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
         return e;
     k_toep_rows_inv<L><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(f);
@@ -538,9 +568,9 @@ static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, float lam, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg,
+cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, const float2* cg_r, CgState* cg,
                             const float* cg_z) {
-    FIRM_SWITCH_2N(2 * P.N, { return toeplitz_l<LL>(P, x, y, lam, cg_r, cg, cg_z); });
+    FIRM_SWITCH_2N(2 * P.N, { return toeplitz_l<LL>(P, x, y, cg_r, cg, cg_z); });
     return cudaErrorInvalidValue;
 }
 
@@ -554,14 +584,16 @@ cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const 
 #define FIRM_SWITCH_N(Nval, ...)                                                              \
     switch (Nval) {                                                                          \
         FIRM_CASE_L(16, __VA_ARGS__) FIRM_CASE_L(32, __VA_ARGS__) FIRM_CASE_L(48, __VA_ARGS__)   \
-        FIRM_CASE_L(64, __VA_ARGS__) FIRM_CASE_L(96, __VA_ARGS__) FIRM_CASE_L(128, __VA_ARGS__)  \
+        FIRM_CASE_L(64, __VA_ARGS__) FIRM_CASE_L(80, __VA_ARGS__) FIRM_CASE_L(96, __VA_ARGS__)   \
+        FIRM_CASE_L(128, __VA_ARGS__)                                                          \
         default: return cudaErrorInvalidValue;                                               \
     }
 
 struct PRowsFwdOp : NoFinish {
-    const double* r; float2* u; const float2* tw; int n_rows, N;
+    const float2* r; float2* u; const float2* tw; int n_rows, N;     // r: double-words
     __device__ __forceinline__ float2 load(int row, int n) const {
-        return make_float2((float)__ldg(&r[(size_t)row * N + n]), 0.0f);
+        const float2 v = __ldg(&r[(size_t)row * N + n]);
+        return make_float2(v.x + v.y, 0.0f);
     }
     __device__ __forceinline__ void store(int row, int k, float2 v) const {
         if (k <= N / 2) u[(size_t)row * (N / 2 + 1) + k] = v;
@@ -587,7 +619,7 @@ __global__ void __launch_bounds__(kThreads) k_pc_z(float2* __restrict__ u, const
 }
 
 template <int L>
-__global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restrict__ u, const double* __restrict__ r,
+__global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restrict__ u, const float2* __restrict__ r,
                                                           float* __restrict__ z, double* red, CgState* cg,
                                                           const float2* __restrict__ tw, int n_rows) {
     // z <- P r; reduces <r, z_new> and <r, z_old> for the flexible (Polak-Ribiere)
@@ -602,25 +634,24 @@ __global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restri
     constexpr int ROWS = rows_per_block<L>();
     const int r0 = blockIdx.x * ROWS;
     const int nl = min(ROWS, n_rows - r0);
-    double acc = 0.0, acc_old = 0.0;
+    float2 acc = make_float2(0.0f, 0.0f), acc_old = make_float2(0.0f, 0.0f);
     auto ld = [&](int line, int n) {
         const float2* row = u + (size_t)(r0 + line) * H;
         return n <= N / 2 ? row[n] : c_conj(row[N - n]);
     };
     auto st = [&](int line, int k, float2 v) {
         const size_t i = (size_t)(r0 + line) * N + k;
-        const double ri = __ldg(&r[i]);
-        acc_old += ri * (double)z[i];
+        const float2 ri = __ldg(&r[i]);
+        acc_old = dw_acc_mul(acc_old, ri, z[i]);
         z[i] = v.x;
-        acc += ri * (double)v.x;
+        acc = dw_acc_mul(acc, ri, v.x);
     };
     block_fft<L, +1, false>(nl, ld, st, S, tw);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        acc += __shfl_down_sync(0xffffffffu, acc, o);
-        acc_old += __shfl_down_sync(0xffffffffu, acc_old, o);
+    const float2 w0 = dw_warp_sum(acc), w1 = dw_warp_sum(acc_old);
+    if ((threadIdx.x & 31) == 0) {
+        s_red[0][threadIdx.x >> 5] = dw_to_double(w0);
+        s_red[1][threadIdx.x >> 5] = dw_to_double(w1);
     }
-    if ((threadIdx.x & 31) == 0) { s_red[0][threadIdx.x >> 5] = acc; s_red[1][threadIdx.x >> 5] = acc_old; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double b0 = 0.0, b1 = 0.0;
@@ -652,6 +683,9 @@ __global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restri
     if (threadIdx.x == 0) {
         const double rz_new = s_fin[0][0], rz_old_new_r = s_fin[1][0];
         cg->beta = cg->first ? 0.0 : fmax(0.0, (rz_new - rz_old_new_r) / cg->rz);
+        const float2 bf = dw_from_double(cg->beta);
+        cg->beta_f[0] = bf.x;
+        cg->beta_f[1] = bf.y;
         cg->rz = rz_new;
         cg->first = 0;
         cg->ticket_c = 0;
@@ -663,7 +697,7 @@ __global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restri
 }
 
 template <int L>
-static cudaError_t precond_l(Plan& P, const double* r, float* z, CgState* cg) {
+static cudaError_t precond_l(Plan& P, const float2* r, float* z, CgState* cg) {
     Workspace& w = P.ws;
     constexpr int N = L, H = L / 2 + 1;
     constexpr int ROWS = rows_per_block<L>();
@@ -693,7 +727,7 @@ static cudaError_t precond_l(Plan& P, const double* r, float* z, CgState* cg) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_precond(Plan& P, const double* r, float* z, CgState* cg) {
+cudaError_t launch_precond(Plan& P, const float2* r, float* z, CgState* cg) {
     FIRM_SWITCH_N(P.N, { return precond_l<LL>(P, r, z, cg); });
     return cudaErrorInvalidValue;
 }
@@ -701,7 +735,7 @@ cudaError_t launch_precond(Plan& P, const double* r, float* z, CgState* cg) {
 // T. Chan's optimal circulant of the Toeplitz operator (the circulant nearest to it in
 // Frobenius norm): column c(m) = sum over n = m (mod N), n in (-N, N)^3, of
 // Ker(n) prod_a (N - |n_a|) / N, read from the Ker half box (Ker(-n) = Ker(n)).
-__global__ void k_chan_column(const float* __restrict__ ker, double* __restrict__ c, int N) {
+__global__ void k_chan_column(const float* __restrict__ ker, float2* __restrict__ c, int N) {
     const long long total = (long long)N * N * N;
     const int N2 = 2 * N;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
@@ -725,7 +759,7 @@ __global__ void k_chan_column(const float* __restrict__ ker, double* __restrict_
                 }
             }
         }
-        c[i] = acc;
+        c[i] = dw_from_double(acc);
     }
 }
 
@@ -851,7 +885,7 @@ static cudaError_t toeplitz_static_l(float2* scratch, const float* khat, const f
         return e;
     k_cols_cg<L, +1, TColsYInvOp><<<N * tiles_b, kThreads, smem_cols, s>>>(d, nullptr);
     const float scale = 1.0f / ((float)L * (float)L * (float)L);
-    TRowsInvOp f{t1, x, y, nullptr, nullptr, tw, N * N, N, scale, lam, nullptr};
+    TRowsInvOp f{t1, x, y, nullptr, nullptr, tw, N * N, N, scale, lam, nullptr, nullptr};
     if ((e = cudaFuncSetAttribute(k_toep_rows_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
         return e;
     k_toep_rows_inv<L><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, s>>>(f);

@@ -15,6 +15,8 @@ constexpr int kBrick = 8;             // spreading brick edge in fine-grid cells
 constexpr int kKbDeg = 7;             // degree of the per-tap window polynomials
 constexpr int kMaxW = 8;              // widest Kaiser-Bessel window supported
 constexpr int kChunk = 8192;          // most points one spreading work item takes
+constexpr int kMinChunk = 1024;       // smallest work-item size a plan may be tuned to
+constexpr int kMaxBatch = 1024;       // most plans one batch holds
 constexpr int kTBits = 13;            // point id = m << kTBits | t (t < 8192)
 constexpr int kMaxHist = 20001;       // residual history capacity (iterations + 1)
 constexpr int kRedSlots = 4096;       // per-block partial sums of a reduction
@@ -49,6 +51,9 @@ struct CgState {
     int first;        // 1 until the first preconditioner application
     unsigned int ticket_c;
     int pad_;
+    double alpha;     // step length of the current iteration (set with pq)
+    float alpha_f[2]; // alpha and beta as double-words (hi, lo) for the vector updates
+    float beta_f[2];
 };
 
 struct Workspace {
@@ -84,7 +89,7 @@ struct Workspace {
     float* rhs = nullptr;           // A*b
     // CG
     float* x = nullptr;
-    double* r = nullptr;            // residual recurrence in FP64
+    float2* r = nullptr;            // residual recurrence, double-word (hi, lo) per element
     float* p = nullptr;
     float* q = nullptr;
     float2* t1 = nullptr;           // N x N x (N+1)
@@ -99,6 +104,7 @@ struct Workspace {
     double* red_b = nullptr;
     double* hist = nullptr;
     CgState* cg = nullptr;
+    float* lam = nullptr;           // device: [0] lam_eff, [1] Ker(0) of the last kernel
     size_t total = 0;
 };
 
@@ -110,6 +116,7 @@ struct Plan {
     Workspace ws;
     int N = 0, Gk = 0, Gr = 0, nH = 0, nK = 0, nbk = 0, nbr = 0, n_ctf = 1;
     size_t max_work = 0;
+    int chunk = kChunk;             // points per spreading work item (kMinChunk..kChunk)
     KbPoly poly{};
     double lam_eff = 0.0;
     float h2_max = 1.0f;           // largest kernel-channel weight (bounds the fixed-point scale)
@@ -148,7 +155,16 @@ double ctf_value(const firm_ctf_group& g, double r_invA);
 // ---- launchers (spread.cu) ----
 cudaError_t launch_geom(const double* R, int M, ImgGeom* geom, cudaStream_t s);
 cudaError_t launch_bin(Plan& P, int M, bool kernel_channel);
-cudaError_t launch_spread(Plan& P, int M, bool kernel_channel);
+cudaError_t launch_spread(Plan& P, int M, bool kernel_channel);        // clear + spread
+cudaError_t launch_spread_clear(Plan& P, bool kernel_channel);          // zero the fine grid
+cudaError_t launch_spread_only(Plan& P, int M, bool kernel_channel);    // spread (grid cleared)
+// One persistent launch spreading the binned points of n plans (same W) into their own
+// fine grids; each plan's grid cleared and its points binned beforehand.  args: device
+// array of n per-plan descriptors; item_off: device (n + 1) ints; queue: device int.
+size_t spread_batch_desc_bytes();
+void spread_batch_fill_desc(Plan& P, bool kernel_channel, void* host_desc);
+cudaError_t launch_spread_batch(int n, bool kernel_channel, int W, const KbPoly& poly, const void* dev_desc,
+                                int* item_off, int* queue, int num_sms, cudaStream_t s);
 
 // ---- launchers (fft_passes.cu) ----
 cudaError_t fft_init_constants();
@@ -156,14 +172,16 @@ cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* s
 cudaError_t launch_ker_transform(Plan& P);     // grid -> Ker half box
 cudaError_t launch_khat(Plan& P);              // Ker -> K-hat
 cudaError_t launch_rhs_transform(Plan& P);     // grid -> A*b
-// Toeplitz apply y = Ker * x + lam x.  With cg != nullptr the first pass forms
-// p = r + beta p in place (x = p, r given) and the last pass reduces <p, y>.
-cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, float lam, const double* cg_r, CgState* cg,
+cudaError_t launch_lam_eff(Plan& P);           // ws.lam from Ker(0) on the device
+// Toeplitz apply y = Ker * x + lam_eff x (lam_eff read from ws.lam).  With cg != nullptr
+// the first pass forms p = r + beta p in place (x = p, r given) and the last pass
+// reduces <p, y>.
+cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, const float2* cg_r, CgState* cg,
                             const float* cg_z = nullptr);
 
 // Preconditioner: z = P r through N^3 FFTs with the Fourier diagonal pc_diag; the last
 // pass reduces <r, z> and sets beta (fft_passes.cu).
-cudaError_t launch_precond(Plan& P, const double* r, float* z, CgState* cg);
+cudaError_t launch_precond(Plan& P, const float2* r, float* z, CgState* cg);
 cudaError_t launch_chan_spectrum(Plan& P);       // T. Chan circulant spectrum into ws.t1 (half spectrum)
 cudaError_t launch_pc_build_circulant(Plan& P);  // pc_diag = 1 / ((kappa + lam_eff) N^3) from ws.t1
 
@@ -178,3 +196,8 @@ cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_t
 cudaError_t launch_cg_update(Plan& P);
 
 }  // namespace firm
+
+// The opaque plan handle of include/firm.h.
+struct firm_plan_s {
+    firm::Plan P;
+};

@@ -179,10 +179,10 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a, int M) {
 }
 
 // Single-block scan over bricks: cursor = exclusive prefix of count; work items
-// (brick, start, length) of at most kChunk points.
+// (brick, start, length) of at most `chunk` points (chunk <= kChunk).
 __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__ count, uint32_t* __restrict__ cursor,
                                                     int nbricks, int4* __restrict__ work, int* __restrict__ counters,
-                                                    int max_work) {
+                                                    int max_work, int chunk) {
     __shared__ unsigned long long s_pts[32];
     __shared__ int s_items[32];
     const int T = blockDim.x, tid = threadIdx.x;
@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__
     for (int b = b0; b < b1; b += 4) {   // nbricks and per are multiples of 4
         const uint4 c4 = *reinterpret_cast<const uint4*>(count + b);
         pts += (unsigned long long)c4.x + c4.y + c4.z + c4.w;
-        items += (int)((c4.x + kChunk - 1) / kChunk) + (int)((c4.y + kChunk - 1) / kChunk) +
-                 (int)((c4.z + kChunk - 1) / kChunk) + (int)((c4.w + kChunk - 1) / kChunk);
+        items += (int)((c4.x + chunk - 1) / chunk) + (int)((c4.y + chunk - 1) / chunk) +
+                 (int)((c4.z + chunk - 1) / chunk) + (int)((c4.w + chunk - 1) / chunk);
     }
     const int lane = tid & 31, wid = tid >> 5;
     unsigned long long ip = pts;
@@ -225,8 +225,8 @@ __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__
     for (int b = b0; b < b1; ++b) {
         const uint32_t c = count[b];
         cursor[b] = (uint32_t)off;
-        for (uint32_t s = 0; s < c; s += kChunk) {
-            if (woff < max_work) work[woff] = make_int4(b, (int)(off + s), (int)min((uint32_t)kChunk, c - s), 0);
+        for (uint32_t s = 0; s < c; s += (uint32_t)chunk) {
+            if (woff < max_work) work[woff] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), 0);
             ++woff;
         }
         off += c;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ paylo
     int* s_pre = reinterpret_cast<int*>(s_mask + kChunk);       // kChunk: A(r)
     uint8_t* s_cls = reinterpret_cast<uint8_t*>(s_pre + kChunk);
     __shared__ int s_hist[32], s_cur[32], s_off[32], s_maxn;
-    __shared__ int s_part[256];
+    __shared__ int s_part[8];
     const int n_work = counters[0];
     for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
         const int4 wk = work[item];
@@ -292,14 +292,19 @@ __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ paylo
             s_mask[r] = m;
             part += __popc(m);
         }
-        s_part[threadIdx.x] = part;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int acc = 0;
-            for (int i = 0; i < (int)blockDim.x; ++i) { const int t = s_part[i]; s_part[i] = acc; acc += t; }
+        // exclusive block scan of the partial sums (warp scans, then the 8 warp totals)
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int incl = part;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
+        if (lane == 31) s_part[wid] = incl;
         __syncthreads();
-        int acc = s_part[threadIdx.x];
+        int wbase = 0;
+        for (int i = 0; i < wid; ++i) wbase += s_part[i];
+        int acc = wbase + incl - part;
         for (int r = r0; r < r1; ++r) { s_pre[r] = acc; acc += __popc(s_mask[r]); }
         __syncthreads();
         for (int i = threadIdx.x; i < len; i += blockDim.x) {
@@ -319,7 +324,8 @@ static void bin_w(Plan& P, const BinArgs& a0, int nbricks) {
     const int M = (int)(a.npts / a.nH);
     const dim3 grid((a.nH + 255) / 256, (unsigned)(M < 65535 ? M : 65535));
     k_bin<W, false><<<grid, 256, 0, P.stream>>>(a, M);
-    k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work);
+    k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work,
+                                          P.chunk);
     a.count = w.cursor;
     k_bin<W, true><<<grid, 256, 0, P.stream>>>(a, M);
     cudaFuncSetAttribute(k_class_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
@@ -347,7 +353,8 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
     a.scale = (float)(G / P.N);
     const long long blocks = (a.npts + 255) / 256;
     if (blocks == 0) {
-        k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work);
+        k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work,
+                                          P.chunk);
         P.launches += 1;
         return cudaGetLastError();
     }
@@ -395,131 +402,203 @@ __device__ __forceinline__ float2 point_weight(const SpreadArgs& a, bool cplx, i
     return make_float2(__ldg(&a.h2[(size_t)g * a.nH + t]), 0.0f);
 }
 
+// One work item (a piece of one brick's points) into the brick's shared-memory region,
+// then the region into the FP64 grid.  lev1/lev2 are zero on entry and on return.
 template <int W, bool CPLX>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
+__device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& poly, const int4 wk, int* lev1,
+                                             float* lev2, float* s_red) {
     constexpr int RG = kBrick + W;
     constexpr int RG3 = RG * RG * RG;
     constexpr int NC = CPLX ? 2 : 1;
     constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
     constexpr int kMagicBits = 0x4B400000;
-    extern __shared__ int sm_i[];
-    int* lev1 = sm_i;                                  // NC * RG3 int32
-    float* lev2 = reinterpret_cast<float*>(sm_i + NC * RG3);   // NC * RG3 float
-    __shared__ int s_item;
-    __shared__ float s_red[kSpreadWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n_work = a.counters[0];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[1], 1);
-        for (int i = threadIdx.x; i < NC * RG3; i += blockDim.x) {
-            lev1[i] = 0;
-            lev2[i] = 0.0f;
+    const int b = wk.x;
+    const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
+    const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * kBrick;
+    // the piece is ordered round-robin over bank classes: thread i takes points
+    // i, i + 256, ... (every thread the same count, up to one)
+    const uint32_t s0 = (uint32_t)wk.y + threadIdx.x;
+    const int my_n = wk.z > (int)threadIdx.x ? (wk.z - (int)threadIdx.x + kSpreadThreads - 1) / kSpreadThreads : 0;
+    float wmax = a.wmax_fixed;
+    if (wmax <= 0.0f) {
+        for (int i = 0; i < my_n; ++i) {
+            const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
+            const float2 wv = point_weight(a, CPLX, (int)(id >> kTBits), (int)(id & ((1u << kTBits) - 1u)));
+            wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        if (lane == 0) s_red[warp] = wmax;
         __syncthreads();
-        const int item = s_item;
-        if (item >= n_work) break;
-        const int4 wk = a.work[item];
-        const int b = wk.x;
-        const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
-        const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * kBrick;
-        // the piece is ordered round-robin over bank classes: thread i takes points
-        // i, i + 256, ... (every thread the same count, up to one)
-        const uint32_t s0 = (uint32_t)wk.y + threadIdx.x;
-        const int my_n = wk.z > (int)threadIdx.x ? (wk.z - (int)threadIdx.x + kSpreadThreads - 1) / kSpreadThreads : 0;
-        float wmax = a.wmax_fixed;
-        if (wmax <= 0.0f) {
-            for (int i = 0; i < my_n; ++i) {
-                const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
-                const float2 wv = point_weight(a, CPLX, (int)(id >> kTBits), (int)(id & ((1u << kTBits) - 1u)));
-                wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+        wmax = s_red[0];
+#pragma unroll
+        for (int i = 1; i < kSpreadWarps; ++i) wmax = fmaxf(wmax, s_red[i]);
+    }
+    const int rounds = (((wk.z + kSpreadThreads - 1) / kSpreadThreads) + 1) / 2;
+    int ex = 0;
+    if (wmax > 0.0f) frexpf(wmax, &ex);                // wmax <= 2^ex
+    const float S = ldexpf(1.0f, 21 - ex), invS = ldexpf(1.0f, ex - 21);
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = 2 * r + q;
+            if (i >= my_n) continue;
+            const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
+            const int m = (int)(id >> kTBits);
+            const int t = (int)(id & ((1u << kTBits) - 1u));
+            const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
+            const int base = region_base<W>(p, lo0, lo1, lo2);
+            if (base < 0) {
+                atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
+                continue;
             }
+            const float2 wv = point_weight(a, CPLX, m, t);
+            float wx[W], wy[W], wz[W];
+            window_taps<W>(poly, p.f[0], wx);
+            window_taps<W>(poly, p.f[1], wy);
+            window_taps<W>(poly, p.f[2], wz);
+            const float wr = wv.x * S, wi = wv.y * S;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-            if (lane == 0) s_red[warp] = wmax;
-            __syncthreads();
-            wmax = s_red[0];
+            for (int dz = 0; dz < W; ++dz) {
+                const float az = wr * wz[dz], bzw = wi * wz[dz];
 #pragma unroll
-            for (int i = 1; i < kSpreadWarps; ++i) wmax = fmaxf(wmax, s_red[i]);
-        }
-        const int rounds = (((wk.z + kSpreadThreads - 1) / kSpreadThreads) + 1) / 2;
-        int ex = 0;
-        if (wmax > 0.0f) frexpf(wmax, &ex);                // wmax <= 2^ex
-        const float S = ldexpf(1.0f, 21 - ex), invS = ldexpf(1.0f, ex - 21);
-        for (int r = 0; r < rounds; ++r) {
+                for (int dy = 0; dy < W; ++dy) {
+                    const float ayz = az * wy[dy], byz = bzw * wy[dy];
+                    int* row = lev1 + base + (dz * RG + dy) * RG;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int i = 2 * r + q;
-                if (i >= my_n) continue;
-                const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
-                const int m = (int)(id >> kTBits);
-                const int t = (int)(id & ((1u << kTBits) - 1u));
-                const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
-                const int base = region_base<W>(p, lo0, lo1, lo2);
-                if (base < 0) {
-                    atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
-                    continue;
-                }
-                const float2 wv = point_weight(a, CPLX, m, t);
-                float wx[W], wy[W], wz[W];
-                window_taps<W>(a.poly, p.f[0], wx);
-                window_taps<W>(a.poly, p.f[1], wy);
-                window_taps<W>(a.poly, p.f[2], wz);
-                const float wr = wv.x * S, wi = wv.y * S;
-#pragma unroll
-                for (int dz = 0; dz < W; ++dz) {
-                    const float az = wr * wz[dz], bzw = wi * wz[dz];
-#pragma unroll
-                    for (int dy = 0; dy < W; ++dy) {
-                        const float ayz = az * wy[dy], byz = bzw * wy[dy];
-                        int* row = lev1 + base + (dz * RG + dy) * RG;
-#pragma unroll
-                        for (int dx = 0; dx < W; ++dx) {
-                            atomicAdd(row + dx, __float_as_int(fmaf(ayz, wx[dx], kMagic)) - kMagicBits);
-                            if (CPLX) atomicAdd(row + RG3 + dx, __float_as_int(fmaf(byz, wx[dx], kMagic)) - kMagicBits);
-                        }
+                    for (int dx = 0; dx < W; ++dx) {
+                        atomicAdd(row + dx, __float_as_int(fmaf(ayz, wx[dx], kMagic)) - kMagicBits);
+                        if (CPLX) atomicAdd(row + RG3 + dx, __float_as_int(fmaf(byz, wx[dx], kMagic)) - kMagicBits);
                     }
                 }
             }
-            __syncthreads();
-            for (int i = threadIdx.x; i < NC * RG3; i += blockDim.x) {
-                const int v = lev1[i];
-                if (v != 0) {
-                    lev2[i] = fmaf((float)v, invS, lev2[i]);
-                    lev1[i] = 0;
-                }
-            }
-            __syncthreads();
         }
-        // add level 2 into the FP64 grid (periodic wrap)
-        const int o0 = lo0 - W / 2, o1 = lo1 - W / 2, o2 = lo2 - W / 2;
-        for (int i = threadIdx.x; i < RG3; i += blockDim.x) {
-            const float vr = lev2[i];
-            const float vi = CPLX ? lev2[RG3 + i] : 0.0f;
-            if (vr == 0.0f && vi == 0.0f) continue;
-            const int rx = i % RG, ry = (i / RG) % RG, rz = i / (RG * RG);
-            int gx = o0 + rx, gy = o1 + ry, gz = o2 + rz;
-            gx += (gx < 0) ? a.G : 0;
-            gx -= (gx >= a.G) ? a.G : 0;
-            gy += (gy < 0) ? a.G : 0;
-            gy -= (gy >= a.G) ? a.G : 0;
-            gz += (gz < 0) ? a.G : 0;
-            gz -= (gz >= a.G) ? a.G : 0;
-            const size_t cell = ((size_t)gz * a.G + gy) * a.G + gx;
-            if (CPLX) {
-                atomicAdd(&a.grid[2 * cell], (double)vr);
-                atomicAdd(&a.grid[2 * cell + 1], (double)vi);
-            } else {
-                atomicAdd(&a.grid[cell], (double)vr);
+        __syncthreads();
+        for (int i = threadIdx.x; i < NC * RG3; i += blockDim.x) {
+            const int v = lev1[i];
+            if (v != 0) {
+                lev2[i] = fmaf((float)v, invS, lev2[i]);
+                lev1[i] = 0;
             }
         }
         __syncthreads();
     }
+    // add level 2 into the FP64 grid (periodic wrap) and clear it
+    const int o0 = lo0 - W / 2, o1 = lo1 - W / 2, o2 = lo2 - W / 2;
+    for (int i = threadIdx.x; i < RG3; i += blockDim.x) {
+        const float vr = lev2[i];
+        const float vi = CPLX ? lev2[RG3 + i] : 0.0f;
+        lev2[i] = 0.0f;
+        if (CPLX) lev2[RG3 + i] = 0.0f;
+        if (vr == 0.0f && vi == 0.0f) continue;
+        const int rx = i % RG, ry = (i / RG) % RG, rz = i / (RG * RG);
+        int gx = o0 + rx, gy = o1 + ry, gz = o2 + rz;
+        gx += (gx < 0) ? a.G : 0;
+        gx -= (gx >= a.G) ? a.G : 0;
+        gy += (gy < 0) ? a.G : 0;
+        gy -= (gy >= a.G) ? a.G : 0;
+        gz += (gz < 0) ? a.G : 0;
+        gz -= (gz >= a.G) ? a.G : 0;
+        const size_t cell = ((size_t)gz * a.G + gy) * a.G + gx;
+        if (CPLX) {
+            atomicAdd(&a.grid[2 * cell], (double)vr);
+            atomicAdd(&a.grid[2 * cell + 1], (double)vi);
+        } else {
+            atomicAdd(&a.grid[cell], (double)vr);
+        }
+    }
+    __syncthreads();
+}
+
+template <int W, bool CPLX>
+__global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
+    constexpr int RG = kBrick + W;
+    constexpr int NC = CPLX ? 2 : 1;
+    extern __shared__ int sm_i[];
+    int* lev1 = sm_i;                                  // NC * RG^3 int32
+    float* lev2 = reinterpret_cast<float*>(sm_i + NC * RG * RG * RG);   // NC * RG^3 float
+    __shared__ int s_item;
+    __shared__ float s_red[kSpreadWarps];
+    for (int i = threadIdx.x; i < 2 * NC * RG * RG * RG; i += blockDim.x) sm_i[i] = 0;
+    const int n_work = a.counters[0];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[1], 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_work) break;
+        spread_piece<W, CPLX>(a, a.poly, a.work[item], lev1, lev2, s_red);
+    }
+}
+
+// Persistent spreading over the work items of several plans: one queue, items of plan
+// p numbered item_off[p] .. item_off[p + 1] - 1 (plans in the order given).
+template <int W, bool CPLX>
+__global__ void __launch_bounds__(kSpreadThreads) k_spread_batch(const SpreadArgs* __restrict__ desc, int n,
+                                                                 const int* __restrict__ item_off, int* queue,
+                                                                 const KbPoly poly) {
+    constexpr int RG = kBrick + W;
+    constexpr int NC = CPLX ? 2 : 1;
+    extern __shared__ int sm_i[];
+    int* lev1 = sm_i;
+    float* lev2 = reinterpret_cast<float*>(sm_i + NC * RG * RG * RG);
+    __shared__ int s_item, s_prob;
+    __shared__ float s_red[kSpreadWarps];
+    for (int i = threadIdx.x; i < 2 * NC * RG * RG * RG; i += blockDim.x) sm_i[i] = 0;
+    const int total = item_off[n];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int g = atomicAdd(queue, 1);
+            int lo = 0, hi = n;                        // last p with item_off[p] <= g
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(&item_off[mid]) <= g) lo = mid; else hi = mid;
+            }
+            s_item = g;
+            s_prob = lo;
+        }
+        __syncthreads();
+        const int g = s_item;
+        if (g >= total) break;
+        const int pi = s_prob;
+        const SpreadArgs a = desc[pi];
+        spread_piece<W, CPLX>(a, poly, a.work[g - __ldg(&item_off[pi])], lev1, lev2, s_red);
+    }
+}
+
+// item_off = exclusive prefix of the plans' work-item counts; queue = 0.  One warp.
+__global__ void k_batch_items(const SpreadArgs* __restrict__ desc, int n, int* __restrict__ item_off, int* queue) {
+    const int lane = threadIdx.x;
+    int carry = 0;
+    for (int p0 = 0; p0 < n; p0 += 32) {
+        const int p = p0 + lane;
+        const int c = p < n ? desc[p].counters[0] : 0;
+        int v = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (p < n) item_off[p] = carry + v - c;
+        carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) {
+        item_off[n] = carry;
+        *queue = 0;
+    }
+}
+
+template <int W, bool CPLX>
+static size_t spread_smem() {
+    constexpr int RG = kBrick + W;
+    return sizeof(int) * RG * RG * RG * (CPLX ? 2 : 1) * 2;
 }
 
 template <int W, bool CPLX>
 static cudaError_t spread_w(Plan& P, const SpreadArgs& a) {
-    constexpr int RG = kBrick + W;
-    const size_t smem = sizeof(int) * RG * RG * RG * (CPLX ? 2 : 1) * 2;
+    const size_t smem = spread_smem<W, CPLX>();
     cudaError_t e = cudaFuncSetAttribute(k_spread<W, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -531,12 +610,24 @@ static cudaError_t spread_w(Plan& P, const SpreadArgs& a) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_spread(Plan& P, int M, bool kc) {
+template <int W, bool CPLX>
+static cudaError_t spread_batch_w(int n, const SpreadArgs* desc, int* item_off, int* queue, const KbPoly& poly,
+                                  int num_sms, cudaStream_t s) {
+    const size_t smem = spread_smem<W, CPLX>();
+    cudaError_t e = cudaFuncSetAttribute(k_spread_batch<W, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_batch<W, CPLX>, kSpreadThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    k_batch_items<<<1, 32, 0, s>>>(desc, n, item_off, queue);
+    k_spread_batch<W, CPLX><<<num_sms * per_sm, kSpreadThreads, smem, s>>>(desc, n, item_off, queue, poly);
+    return cudaGetLastError();
+}
+
+static SpreadArgs spread_args(Plan& P, bool kc) {
     Workspace& w = P.ws;
     const int G = kc ? P.Gk : P.Gr;
-    const size_t cells = (size_t)G * G * G * (kc ? 1 : 2);
-    cudaError_t e = cudaMemsetAsync(w.grid, 0, sizeof(double) * cells, P.stream);
-    if (e != cudaSuccess || M <= 0) return e;
     SpreadArgs a;
     a.payload = w.payload;
     a.work = w.work;
@@ -555,10 +646,48 @@ cudaError_t launch_spread(Plan& P, int M, bool kc) {
     a.scale = (float)(G / P.N);
     a.wmax_fixed = kc ? P.h2_max : 0.0f;
     a.poly = P.poly;
+    return a;
+}
+
+cudaError_t launch_spread_clear(Plan& P, bool kc) {
+    const int G = kc ? P.Gk : P.Gr;
+    const size_t cells = (size_t)G * G * G * (kc ? 1 : 2);
+    return cudaMemsetAsync(P.ws.grid, 0, sizeof(double) * cells, P.stream);
+}
+
+cudaError_t launch_spread_only(Plan& P, int M, bool kc) {
+    if (M <= 0) return cudaSuccess;
+    const SpreadArgs a = spread_args(P, kc);
     switch (P.p.W) {
         case 6: return kc ? spread_w<6, false>(P, a) : spread_w<6, true>(P, a);
         case 7: return kc ? spread_w<7, false>(P, a) : spread_w<7, true>(P, a);
         case 8: return kc ? spread_w<8, false>(P, a) : spread_w<8, true>(P, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_spread(Plan& P, int M, bool kc) {
+    cudaError_t e = launch_spread_clear(P, kc);
+    if (e != cudaSuccess) return e;
+    return launch_spread_only(P, M, kc);
+}
+
+size_t spread_batch_desc_bytes() { return sizeof(SpreadArgs); }
+
+void spread_batch_fill_desc(Plan& P, bool kc, void* host_desc) {
+    *reinterpret_cast<SpreadArgs*>(host_desc) = spread_args(P, kc);
+}
+
+cudaError_t launch_spread_batch(int n, bool kc, int W, const KbPoly& poly, const void* dev_desc, int* item_off,
+                                int* queue, int num_sms, cudaStream_t s) {
+    const SpreadArgs* d = reinterpret_cast<const SpreadArgs*>(dev_desc);
+    switch (W) {
+        case 6: return kc ? spread_batch_w<6, false>(n, d, item_off, queue, poly, num_sms, s)
+                          : spread_batch_w<6, true>(n, d, item_off, queue, poly, num_sms, s);
+        case 7: return kc ? spread_batch_w<7, false>(n, d, item_off, queue, poly, num_sms, s)
+                          : spread_batch_w<7, true>(n, d, item_off, queue, poly, num_sms, s);
+        case 8: return kc ? spread_batch_w<8, false>(n, d, item_off, queue, poly, num_sms, s)
+                          : spread_batch_w<8, true>(n, d, item_off, queue, poly, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }

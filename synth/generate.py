@@ -246,3 +246,32 @@ def config_inputs(name: str, M: int | None = None, N: int | None = None, images:
         out["images"] = noisy.astype(image_dtype, copy=False)
         out["noise_sigma"] = sigma
     return out
+
+
+# The batched workload: 64 independent reconstructions of uneven size.
+BATCH = dict(n=64, N_choices=(48, 64, 80, 96), M_range=(1000, 8000), n_blobs=30, shift_px=2.0,
+             defocus_um=(1.5, 2.0, 2.5, 3.0), snr=0.1, lam=1e-3, iters=25, seed0=31)
+
+
+def batch_inputs(j: int, images: bool = True, image_dtype=np.float32) -> dict:
+    """Problem j of the batched workload: N uniform over {48, 64, 80, 96}, M uniform in
+    [1000, 8000], its own 30-blob phantom, views as the N=64 workload (70% von
+    Mises-Fisher about 3 axes, 30% Haar), shifts U[-2, 2] px, 1-4 of the 4 defocus
+    groups, SNR 0.1.  Seeds 31 + j."""
+    rng = np.random.default_rng(BATCH["seed0"] + j)
+    N = int(rng.choice(BATCH["N_choices"]))
+    M = int(rng.integers(BATCH["M_range"][0], BATCH["M_range"][1] + 1))
+    blobs = phantom_blobs(BATCH["n_blobs"], N, rng)
+    R = mixed_rotations(M, rng)
+    shifts = uniform_shifts(M, rng, BATCH["shift_px"])
+    ng = int(rng.integers(1, 5))
+    dfs = sorted(rng.choice(BATCH["defocus_um"], ng, replace=False))
+    groups = ctf_group_table(dfs)
+    gid = rng.integers(0, ng, M).astype(np.int32)
+    out = dict(N=N, M=M, R=R, shifts=shifts, groups=groups, group_id=gid, blobs=blobs)
+    if images:
+        clean = project_blobs(blobs, R, N, shifts, dtype=np.float32)
+        noisy, sigma = add_noise(clean, BATCH["snr"], rng)
+        out["images"] = noisy.astype(image_dtype, copy=False)
+        out["noise_sigma"] = sigma
+    return out

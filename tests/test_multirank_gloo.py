@@ -1,0 +1,60 @@
+"""Two CPU ranks (gloo): Ker and A*b are sums over images (eq. kernel, eq. backprojection,
+Section 3.4), so splitting the images across ranks and adding the ranks' partial sums
+with one all-reduce gives the single-process result.  This is the additivity a
+sharded reconstruction would rely on; the benchmark's multi-GPU mode runs replicas
+and reduces only its timings, which the second test checks (max over ranks)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as tmp
+
+import oracle as O
+import synth
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out_path):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inp = synth.config_inputs("C2", M=24, N=8)
+        N, M = inp["N"], inp["M"]
+        K = O.disc(N)
+        h = O.ctf_weights(N, K, inp["groups"], inp["group_id"])
+        a, b = rank * M // world, (rank + 1) * M // world
+        ker = O.kernel(inp["R"][a:b], h[a:b], K, N).real
+        rhs = O.backproject(inp["images"][a:b].astype(np.float64), inp["shifts"][a:b], inp["R"][a:b], h[a:b], K)
+        t = torch.from_numpy(np.concatenate([ker.ravel(), rhs.ravel()]))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        # timing reduction of the benchmark: max over ranks
+        ms = torch.tensor([10.0 + rank])
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        if rank == 0:
+            np.savez(out_path, sums=t.numpy(), ms=ms.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2])
+def test_image_shards_add_up_over_gloo_ranks(tmp_path, world):
+    out = str(tmp_path / "sums.npz")
+    tmp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    got = np.load(out)
+    inp = synth.config_inputs("C2", M=24, N=8)
+    N = inp["N"]
+    K = O.disc(N)
+    h = O.ctf_weights(N, K, inp["groups"], inp["group_id"])
+    ker = O.kernel(inp["R"], h, K, N).real
+    rhs = O.backproject(inp["images"].astype(np.float64), inp["shifts"], inp["R"], h, K)
+    ref = np.concatenate([ker.ravel(), rhs.ravel()])
+    assert np.linalg.norm(got["sums"] - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert float(got["ms"][0]) == 10.0 + world - 1

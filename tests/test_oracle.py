@@ -506,3 +506,60 @@ def test_c1_volume_sensitivity_to_rhs_perturbation():
         x1, _, _ = O.cg(op, rhs + g, 10)
         amp.append(np.linalg.norm(x1 - x0) / np.linalg.norm(x0) / 1e-5)
     assert 10 <= min(amp) and max(amp) <= 40, amp
+
+
+def test_chunked_voxel_sums_equal_the_full_sums():
+    """sums_at_voxels (per-group weights, chunks of images) equals eq. kernel and
+    eq. backprojection evaluated by the full-array oracle at the same voxels, and the
+    shards of an image set add up."""
+    inp = synth.config_inputs("C2", M=30, N=8)
+    N, M = inp["N"], inp["M"]
+    K = O.disc(N)
+    hg = O.ctf_weights(N, K, inp["groups"], np.arange(inp["groups"].shape[0], dtype=np.int32))
+    h = O.ctf_weights(N, K, inp["groups"], inp["group_id"])
+    vox = np.array([[0, 0, 0], [1, -2, 3], [-4, 3, 0], [3, 3, -4]])
+    imgs = inp["images"].astype(np.float64)
+    parts = [O.sums_at_voxels(inp["R"][a:b], inp["group_id"][a:b], hg, imgs[a:b], inp["shifts"][a:b], K, N, vox)
+             for a, b in ((0, 11), (11, 30))]
+    ker = parts[0][0] + parts[1][0]
+    rhs = parts[0][1] + parts[1][1]
+    Kfull = O.kernel(inp["R"], h, K, N)
+    A = O.adjoint(O.image_dft(imgs, K, inp["shifts"]), inp["R"], h, K, N)
+    for i, (n1, n2, n3) in enumerate(vox):
+        assert abs(ker[i] - Kfull[n3 + N, n2 + N, n1 + N]) <= 1e-10 * abs(Kfull).max()
+        assert abs(rhs[i] - A[n3 + N // 2, n2 + N // 2, n1 + N // 2]) <= 1e-10 * abs(A).max()
+    assert abs(parts[0][2] + parts[1][2] - (h * h).sum()) <= 1e-10 * (h * h).sum()
+
+
+def test_cg_trajectory_horizon_under_tiny_operator_noise():
+    """Section 3.3 CG on a CTF-weighted problem (N=16, 60 views, 2 defocus groups,
+    lambda = 1e-3 Ker(0)): a relative perturbation of 1e-9 of every operator apply moves
+    the oracle's own FP64 iterate by < 1e-6 after 10 iterations but by > 1e-3 after 25
+    (the iterate of a fixed, large iteration count is not a stable quantity; the FP32
+    path's ~1e-7 rounding moves it by ~4e-2).  This fixes how many iterations a parity
+    test of the iterate itself can span."""
+    inp = synth.config_inputs("C2", M=60, N=16)
+    rng = np.random.default_rng(100)
+    sub = rng.choice(inp["groups"].shape[0], 2, replace=False)
+    groups = inp["groups"][sub]
+    gid = rng.integers(0, 2, 60).astype(np.int32)
+    N = 16
+    K = O.disc(N)
+    h = O.ctf_weights(N, K, groups, gid)
+    Ker = O.kernel(inp["R"], h, K, N).real
+    rhs = O.backproject(inp["images"].astype(np.float64), inp["shifts"], inp["R"], h, K)
+    lam = O.lambda_eff(1e-3, 0, Ker[N, N, N])
+    Kh = O.khat(Ker).real
+    op = lambda v: O.toeplitz_apply(Kh, v, lam).real
+    noise = np.random.default_rng(9)
+
+    def noisy(v):
+        q = op(v)
+        return q + 1e-9 * np.abs(q).mean() * noise.standard_normal(q.shape)
+
+    dev = {}
+    for it in (10, 25):
+        xa, _, _ = O.cg(op, rhs, it)
+        xb, _, _ = O.cg(noisy, rhs, it)
+        dev[it] = np.linalg.norm(xb - xa) / np.linalg.norm(xa)
+    assert dev[10] < 1e-6 and dev[25] > 1e-3, dev
