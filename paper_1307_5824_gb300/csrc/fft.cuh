@@ -227,6 +227,52 @@ __device__ __forceinline__ void fft_step2(int nl, St& st, const float2* S) {
     }
 }
 
+// Step 1 with a hook run once per item after all of its loads: a loader that also
+// writes back (the CG direction update) keeps its loads pure, so they are all in
+// flight together, and does its stores in the hook.
+template <int L, int SIGN, bool LINE_FAST, class Ld, class Post>
+__device__ __forceinline__ void fft_step1_post(int nl, Ld& ld, Post& post, float2* S, const float2* __restrict__ tw) {
+    constexpr int L1 = Split<L>::L1, L2 = Split<L>::L2;
+    for (int it = threadIdx.x; it < nl * L2; it += blockDim.x) {
+        const int line = LINE_FAST ? it % nl : it / L2;
+        const int n2 = LINE_FAST ? it / nl : it % L2;
+        float2 a[L1];
+#pragma unroll
+        for (int n1 = 0; n1 < L1; ++n1) a[n1] = ld(line, L2 * n1 + n2);
+#pragma unroll
+        for (int n1 = 0; n1 < L1; ++n1) post(line, L2 * n1 + n2, a[n1]);
+        Dft<L1, SIGN>::run(a);
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            float2 v = a[k1];
+            if (k1 != 0 && n2 != 0) v = c_mul_tw<SIGN>(v, __ldg(&tw[n2 * k1]));
+            S[sidx<L, LINE_FAST>(line, k1, n2, nl)] = v;
+        }
+    }
+}
+
+// Step 2 with per-output operands fetched before the DFT: pre(line, k) is issued for
+// all L2 outputs of an item first (independent loads in flight together), then
+// st(line, k, value, pre(line, k)).
+template <int L, int SIGN, bool LINE_FAST, class Pre, class St>
+__device__ __forceinline__ void fft_step2_pre(int nl, Pre& pre, St& st, const float2* S) {
+    constexpr int L1 = Split<L>::L1, L2 = Split<L>::L2;
+    using PV = decltype(pre(0, 0));
+    for (int it = threadIdx.x; it < nl * L1; it += blockDim.x) {
+        const int line = LINE_FAST ? it % nl : it / L1;
+        const int k1 = LINE_FAST ? it / nl : it % L1;
+        PV pv[L2];
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) pv[k2] = pre(line, k1 + L1 * k2);
+        float2 b[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) b[n2] = S[sidx<L, LINE_FAST>(line, k1, n2, nl)];
+        Dft<L2, SIGN>::run(b);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) st(line, k1 + L1 * k2, b[k2], pv[k2]);
+    }
+}
+
 template <int L, int SIGN, bool LINE_FAST, class Ld, class St>
 __device__ __forceinline__ void block_fft(int nl, Ld& ld, St& st, float2* S, const float2* __restrict__ tw) {
     fft_step1<L, SIGN, LINE_FAST>(nl, ld, S, tw);

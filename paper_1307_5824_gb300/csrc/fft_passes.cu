@@ -94,6 +94,8 @@ static cudaError_t run_rows(const Op& op, cudaStream_t s) {
 
 struct NoFinish {
     __device__ __forceinline__ void finish() const {}
+    __device__ __forceinline__ void prepare() {}                       // per-block scalars
+    __device__ __forceinline__ void post(int, int, float2) const {}    // after an item's loads
 };
 
 // Transform lengths instantiated: 2N and 4N for N in {16, 32, 48, 64, 80, 96, 128}.
@@ -375,19 +377,24 @@ cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* s
 struct TRowsFwdOp : NoFinish {
     const float* x; float* p; const float2* r; const CgState* cg; float2* out; const float2* tw; int n_rows, N;
     const float* z = nullptr;   // preconditioned residual: p = z + beta p when set
+    float bh = 0.0f, bl = 0.0f; // beta as a double-word, read once per block
+    __device__ __forceinline__ void prepare() {
+        if (cg) { bh = cg->beta_f[0]; bl = cg->beta_f[1]; }
+    }
     __device__ __forceinline__ float2 load(int row, int n) const {
         if (n >= N) return make_float2(0.0f, 0.0f);
         const size_t i = (size_t)row * N + n;
-        if (cg) {   // p = r + beta p (r, beta double-words) or p = z + beta p, written back
-            const float pv = p[i];
-            float bh, bl;
-            if (z) { bh = __ldg(&z[i]); bl = 0.0f; }
-            else { const float2 rv = __ldg(&r[i]); bh = rv.x; bl = rv.y; }
-            const float v = fmaf(cg->beta_f[0], pv, bh) + fmaf(cg->beta_f[1], pv, bl);
-            p[i] = v;
-            return make_float2(v, 0.0f);
+        if (cg) {   // p = r + beta p (r, beta double-words) or p = z + beta p; stored by post()
+            const float pv = __ldg(&p[i]);
+            float ah, al;
+            if (z) { ah = __ldg(&z[i]); al = 0.0f; }
+            else { const float2 rv = __ldg(&r[i]); ah = rv.x; al = rv.y; }
+            return make_float2(fmaf(bh, pv, ah) + fmaf(bl, pv, al), 0.0f);
         }
         return make_float2(__ldg(&x[i]), 0.0f);
+    }
+    __device__ __forceinline__ void post(int row, int n, float2 v) const {
+        if (cg && n < N) p[(size_t)row * N + n] = v.x;
     }
     __device__ __forceinline__ void store(int row, int k, float2 v) const {
         if (k <= N) out[(size_t)row * (N + 1) + k] = v;
@@ -416,16 +423,20 @@ struct TRowsInvOp {
     int n_rows, N; float scale, lam;
     const float* lam_p;   // device lam_eff (overrides lam when set)
     float2* acc;   // per-thread partial <x, y> (CG), double-word
+    __device__ __forceinline__ void prepare() {
+        if (lam_p) lam = __ldg(lam_p);
+    }
     __device__ __forceinline__ float2 load(int row, int n) const {
         const float2* rr = in + (size_t)row * (N + 1);
         return n <= N ? __ldg(&rr[n]) : c_conj(__ldg(&rr[2 * N - n]));
     }
-    __device__ __forceinline__ void store(int row, int k, float2 v) const {
+    __device__ __forceinline__ float pre(int row, int k) const {
+        return k < N ? __ldg(&x[(size_t)row * N + k]) : 0.0f;
+    }
+    __device__ __forceinline__ void store(int row, int k, float2 v, float xv) const {
         if (k >= N) return;
-        const size_t i = (size_t)row * N + k;
-        const float xv = __ldg(&x[i]);
-        const float yv = fmaf(v.x, scale, (lam_p ? __ldg(lam_p) : lam) * xv);
-        y[i] = yv;
+        const float yv = fmaf(v.x, scale, lam * xv);
+        y[(size_t)row * N + k] = yv;
         if (cg) *acc = dw_acc_prod(*acc, xv, yv);
     }
     __device__ __forceinline__ void finish() const {}
@@ -461,10 +472,14 @@ __global__ void __launch_bounds__(kThreads) k_toep_rows_inv(TRowsInvOp op) {
     const int r0 = blockIdx.x * ROWS;
     const int nl = min(ROWS, op.n_rows - r0);
     float2 acc = make_float2(0.0f, 0.0f);
+    op.prepare();
     op.acc = &acc;
     auto ld = [&](int line, int n) { return op.load(r0 + line, n); };
-    auto st = [&](int line, int k, float2 v) { op.store(r0 + line, k, v); };
-    block_fft<L, +1, false>(nl, ld, st, S, op.tw);
+    auto pre = [&](int line, int k) { return op.pre(r0 + line, k); };
+    auto st = [&](int line, int k, float2 v, float xv) { op.store(r0 + line, k, v, xv); };
+    fft_step1<L, +1, false>(nl, ld, S, op.tw);
+    __syncthreads();
+    fft_step2_pre<L, +1, false>(nl, pre, st, S);
     if (!op.cg) return;
     // block reduction
     const float2 wsum = dw_warp_sum(acc);
@@ -511,9 +526,13 @@ __global__ void __launch_bounds__(kThreads) k_rows_cg(Op op, const CgState* cg) 
     constexpr int ROWS = rows_per_block<L>();
     const int r0 = blockIdx.x * ROWS;
     const int nl = min(ROWS, op.n_rows - r0);
+    op.prepare();
     auto ld = [&](int line, int n) { return op.load(r0 + line, n); };
+    auto post = [&](int line, int n, float2 v) { op.post(r0 + line, n, v); };
     auto st = [&](int line, int k, float2 v) { op.store(r0 + line, k, v); };
-    block_fft<L, -1, false>(nl, ld, st, S, op.tw);
+    fft_step1_post<L, -1, false>(nl, ld, post, S, op.tw);
+    __syncthreads();
+    fft_step2<L, -1, false>(nl, st, S);
 }
 
 template <int L, int SIGN, class Op>
@@ -639,14 +658,20 @@ __global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restri
         const float2* row = u + (size_t)(r0 + line) * H;
         return n <= N / 2 ? row[n] : c_conj(row[N - n]);
     };
-    auto st = [&](int line, int k, float2 v) {
+    auto pre = [&](int line, int k) {       // r (double-word) and the previous z
         const size_t i = (size_t)(r0 + line) * N + k;
         const float2 ri = __ldg(&r[i]);
-        acc_old = dw_acc_mul(acc_old, ri, z[i]);
-        z[i] = v.x;
+        return make_float3(ri.x, ri.y, z[i]);
+    };
+    auto st = [&](int line, int k, float2 v, float3 rz) {
+        const float2 ri = make_float2(rz.x, rz.y);
+        acc_old = dw_acc_mul(acc_old, ri, rz.z);
+        z[(size_t)(r0 + line) * N + k] = v.x;
         acc = dw_acc_mul(acc, ri, v.x);
     };
-    block_fft<L, +1, false>(nl, ld, st, S, tw);
+    fft_step1<L, +1, false>(nl, ld, S, tw);
+    __syncthreads();
+    fft_step2_pre<L, +1, false>(nl, pre, st, S);
     const float2 w0 = dw_warp_sum(acc), w1 = dw_warp_sum(acc_old);
     if ((threadIdx.x & 31) == 0) {
         s_red[0][threadIdx.x >> 5] = dw_to_double(w0);

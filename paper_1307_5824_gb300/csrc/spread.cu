@@ -242,15 +242,18 @@ __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__
 // A(r) = sum over r' < r of #{c : n_c > r'}.  Any 32 consecutive points then belong to
 // (almost always) 32 different classes, so the spreading threads can take the piece
 // in order -- every thread the same number of points -- and a warp's 32 atomics of a
-// tap step still hit 32 different banks.
-constexpr int kSortSmem = kChunk * (4 + 4 + 4 + 1);     // ids, masks, prefix, classes
+// tap step still hit 32 different banks.  A piece whose largest class exceeds
+// kSortLevels points (a very skewed piece) is only grouped by class: any order is
+// correct, this one just conflicts more.
+constexpr int kSortLevels = 1024;
+constexpr int kSortSmem = kChunk * (4 + 1) + kSortLevels * (4 + 4);   // ids, classes, masks, prefix
 __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ payload, const uint8_t* __restrict__ cls,
                                                     const int4* __restrict__ work, const int* __restrict__ counters) {
     extern __shared__ uint32_t sm_u[];
-    uint32_t* s_ids = sm_u;                                     // kChunk
-    uint32_t* s_mask = s_ids + kChunk;                          // kChunk: classes with n_c > r
-    int* s_pre = reinterpret_cast<int*>(s_mask + kChunk);       // kChunk: A(r)
-    uint8_t* s_cls = reinterpret_cast<uint8_t*>(s_pre + kChunk);
+    uint32_t* s_ids = sm_u;                                         // kChunk
+    uint32_t* s_mask = s_ids + kChunk;                              // kSortLevels: classes with n_c > r
+    int* s_pre = reinterpret_cast<int*>(s_mask + kSortLevels);      // kSortLevels: A(r)
+    uint8_t* s_cls = reinterpret_cast<uint8_t*>(s_pre + kSortLevels);
     __shared__ int s_hist[32], s_cur[32], s_off[32], s_maxn;
     __shared__ int s_part[8];
     const int n_work = counters[0];
@@ -281,36 +284,43 @@ __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ paylo
         }
         __syncthreads();
         const int maxn = s_maxn;
-        // masks and per-thread partial sums of their popcounts (contiguous r ranges)
-        const int per = (maxn + blockDim.x - 1) / blockDim.x;
-        const int r0 = threadIdx.x * per, r1 = min(maxn, r0 + per);
-        int part = 0;
-        for (int r = r0; r < r1; ++r) {
-            uint32_t m = 0;
+        const bool interleave = maxn <= kSortLevels;
+        if (interleave) {
+            // masks and per-thread partial sums of their popcounts (contiguous r ranges)
+            const int per = (maxn + blockDim.x - 1) / blockDim.x;
+            const int r0 = threadIdx.x * per, r1 = min(maxn, r0 + per);
+            int part = 0;
+            for (int r = r0; r < r1; ++r) {
+                uint32_t m = 0;
 #pragma unroll 8
-            for (int c = 0; c < 32; ++c) m |= (uint32_t)(s_hist[c] > r) << c;
-            s_mask[r] = m;
-            part += __popc(m);
-        }
-        // exclusive block scan of the partial sums (warp scans, then the 8 warp totals)
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        int incl = part;
+                for (int c = 0; c < 32; ++c) m |= (uint32_t)(s_hist[c] > r) << c;
+                s_mask[r] = m;
+                part += __popc(m);
+            }
+            // exclusive block scan of the partial sums (warp scans, then the 8 warp totals)
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+            int incl = part;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane == 31) s_part[wid] = incl;
+            __syncthreads();
+            int wbase = 0;
+            for (int i = 0; i < wid; ++i) wbase += s_part[i];
+            int acc = wbase + incl - part;
+            for (int r = r0; r < r1; ++r) { s_pre[r] = acc; acc += __popc(s_mask[r]); }
         }
-        if (lane == 31) s_part[wid] = incl;
-        __syncthreads();
-        int wbase = 0;
-        for (int i = 0; i < wid; ++i) wbase += s_part[i];
-        int acc = wbase + incl - part;
-        for (int r = r0; r < r1; ++r) { s_pre[r] = acc; acc += __popc(s_mask[r]); }
         __syncthreads();
         for (int i = threadIdx.x; i < len; i += blockDim.x) {
             const int c = s_cls[i];
-            const int r = atomicAdd(&s_cur[c], 1) - s_off[c];
-            const int pos = s_pre[r] + __popc(s_mask[r] & ((1u << c) - 1u));
+            const int k = atomicAdd(&s_cur[c], 1);
+            int pos = k;                                        // grouped by class
+            if (interleave) {
+                const int r = k - s_off[c];
+                pos = s_pre[r] + __popc(s_mask[r] & ((1u << c) - 1u));
+            }
             payload[wk.y + pos] = s_ids[i];
         }
         __syncthreads();
@@ -329,7 +339,7 @@ static void bin_w(Plan& P, const BinArgs& a0, int nbricks) {
     a.count = w.cursor;
     k_bin<W, true><<<grid, 256, 0, P.stream>>>(a, M);
     cudaFuncSetAttribute(k_class_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
-    k_class_sort<<<P.num_sms * 2, 256, kSortSmem, P.stream>>>(w.payload, w.cls, w.work, w.counters);
+    k_class_sort<<<P.num_sms * 4, 256, kSortSmem, P.stream>>>(w.payload, w.cls, w.work, w.counters);
 }
 
 cudaError_t launch_bin(Plan& P, int M, bool kc) {
