@@ -83,8 +83,18 @@ typedef struct {
     int lambda_mode;  /* FIRM_LAMBDA_RELATIVE: lam_eff = lambda * Ker(0); ABSOLUTE: lambda */
     int disc_mode;    /* 0: symmetric disc |k| <= N/2 (the only mode of the CUDA path) */
     int img_dtype;    /* FIRM_IMG_F32 or FIRM_IMG_BF16 */
-    int flags;        /* reserved, must be 0 */
+    int flags;        /* 0, or FIRM_FLAG_FP64_CG */
 } firm_params;
+
+/* FIRM_FLAG_FP64_CG: firm_cg_solve runs CG (Section 3.3) with FP64 vectors and an FP64
+ * Toeplitz apply (eq. property through the 2N circulant of Section 3.2, K-hat recomputed
+ * in FP64 by firm_kernel).  N must be 16, 32 or 64; plain CG only (a preconditioner
+ * set with firm_set_precond makes firm_cg_solve return FIRM_EINVAL); not accepted by
+ * firm_batch_create.  Ker and A*b still come from the FP32 NUFFT.  A long fixed-count
+ * CG iterate is sensitive to the ~1e-7 rounding of FP32 FFTs; this mode removes that
+ * rounding from the solve, at FP64 speed.  The workspace grows by about
+ * (2N)^3 * 24 + N^3 * 32 bytes. */
+enum { FIRM_FLAG_FP64_CG = 1 };
 
 typedef struct firm_plan_s* firm_plan_t;
 

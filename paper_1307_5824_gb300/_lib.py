@@ -20,6 +20,7 @@ FIRM_LAMBDA_RELATIVE, FIRM_LAMBDA_ABSOLUTE = 0, 1
 FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES = 0, 1, 2, 3
 FIRM_PRECOND_NONE, FIRM_PRECOND_CIRCULANT, FIRM_PRECOND_BINNED, FIRM_PRECOND_TABLE = 0, 1, 2, 3
 FIRM_BATCH_GRAPH, FIRM_BATCH_PERSISTENT = 1, 2
+FIRM_FLAG_FP64_CG = 1
 
 EXPORTED = [
     "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_cg_solve",

@@ -202,6 +202,15 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.hist = c.take<double>(kMaxHist);
     w.cg = c.take<CgState>(1);
     w.lam = c.take<float>(2);
+    const bool fp64 = (p.flags & FIRM_FLAG_FP64_CG) != 0;
+    const size_t L3 = fp64 ? 8 * N3 : 0, n64 = fp64 ? N3 : 0;
+    w.tw64 = c.take<double2>(fp64 ? N : 0);
+    w.khat64 = c.take<double>(L3);
+    w.c64 = c.take<double2>(L3);
+    w.x64 = c.take<double>(n64);
+    w.r64 = c.take<double>(n64);
+    w.p64 = c.take<double>(n64);
+    w.q64 = c.take<double>(n64);
     w.total = c.off + 256;
     return w.total;
 }
@@ -216,7 +225,8 @@ static int check_params(const firm_params* p) {
     if (p->M < 0 || p->n_groups < 0) return FIRM_EINVAL;
     if (p->W < 6 || p->W > 8) return FIRM_EINVAL;
     if (p->sigma != 2.0) return FIRM_EINVAL;
-    if (p->disc_mode != 0 || p->flags != 0) return FIRM_EINVAL;
+    if (p->disc_mode != 0 || (p->flags & ~FIRM_FLAG_FP64_CG) != 0) return FIRM_EINVAL;
+    if ((p->flags & FIRM_FLAG_FP64_CG) && p->N != 16 && p->N != 32 && p->N != 64) return FIRM_EINVAL;
     if (p->img_dtype != FIRM_IMG_F32 && p->img_dtype != FIRM_IMG_BF16) return FIRM_EINVAL;
     if (p->lambda_mode != FIRM_LAMBDA_RELATIVE && p->lambda_mode != FIRM_LAMBDA_ABSOLUTE) return FIRM_EINVAL;
     if (!(p->lambda >= 0.0)) return FIRM_EINVAL;
@@ -341,6 +351,44 @@ static int build_preconditioner(Plan& P) {
     return FIRM_OK;
 }
 
+// CG in the FP64 mode (FIRM_FLAG_FP64_CG): plain CG only; same stopping rule and
+// outputs as the FP32 path.
+static int cg_solve_fp64(Plan& P, const float* rd, float* x, int max_iter, double rel_tol, double* resid_hist,
+                         int* iters_out, StageTimer& tm) {
+    if (P.pc_mode != FIRM_PRECOND_NONE) return FIRM_EINVAL;
+    Workspace& w = P.ws;
+    const size_t n = (size_t)P.N * P.N * P.N;
+    const int batch = 8;
+    FIRM_CK(launch_cg64(P, rd, max_iter, rel_tol, 0, 0));
+    for (int it = 0; it < max_iter; it += batch) {
+        FIRM_CK(launch_cg64(P, rd, max_iter, rel_tol, 1, std::min(batch, max_iter - it)));
+        if (rel_tol > 0.0 && it + batch < max_iter) {
+            int done = 0;
+            FIRM_CK(cudaMemcpyAsync(&done, &w.cg->done, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+            FIRM_CK(cudaStreamSynchronize(P.stream));
+            if (done) break;
+        }
+    }
+    FIRM_CK(launch_cg64_result(P));
+    tm.stop();
+    CgState s;
+    FIRM_CK(cudaMemcpyAsync(&s, w.cg, sizeof(CgState), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    P.cg_iters = s.it;
+    if (resid_hist) {
+        const bool dev = is_device(resid_hist);
+        FIRM_CK(cudaMemcpyAsync(resid_hist, w.hist, sizeof(double) * (s.it + 1),
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P.stream));
+    }
+    if (iters_out) *iters_out = s.it;
+    int st = put_out(x, w.x, n * sizeof(float), P.stream);
+    if (st != FIRM_OK) return st;
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    if (s.status != FIRM_OK) return s.status;
+    if (rel_tol > 0.0 && !(s.rr >= 0.0 && std::sqrt(s.rr) <= s.tol)) return FIRM_ENOTCONV;
+    return FIRM_OK;
+}
+
 }  // namespace firm
 
 using namespace firm;
@@ -444,6 +492,14 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
     cp(w.tw_4n, t4.data(), sizeof(float2) * 4 * N);
     cp(w.dec_k, dk.data(), sizeof(float) * dk.size());
     cp(w.dec_r, dr.data(), sizeof(float) * dr.size());
+    std::vector<double2> t64;
+    if (p->flags & FIRM_FLAG_FP64_CG) {
+        for (int j = 0; j < N; ++j) {
+            const double a = -2.0 * kPi * j / (2 * N);
+            t64.push_back(make_double2(std::cos(a), std::sin(a)));
+        }
+        cp(w.tw64, t64.data(), sizeof(double2) * t64.size());
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), P.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
     if (e != cudaSuccess) {
@@ -479,6 +535,7 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     tm.start(3);
     FIRM_CK(launch_khat(P));
     FIRM_CK(launch_lam_eff(P));
+    if (P.p.flags & FIRM_FLAG_FP64_CG) FIRM_CK(launch_khat64(P));
     tm.stop();
     // lam_eff from Ker(0) (the n = 0 entry of the half box), also kept on the host
     float ker0 = 0.f;
@@ -566,6 +623,7 @@ int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, do
     StageTimer tm(P);
     tm.start(8);
     const bool use_pc = P.pc_mode != FIRM_PRECOND_NONE;
+    if (P.p.flags & FIRM_FLAG_FP64_CG) return cg_solve_fp64(P, rd, x, max_iter, rel_tol, resid_hist, iters_out, tm);
     if (use_pc && !P.pc_ready) {
         int st = build_preconditioner(P);
         if (st != FIRM_OK) return st;

@@ -308,6 +308,7 @@ int firm_batch_create(firm_batch_t* out, int n_plans, const firm_plan_t* plans, 
     for (int i = 0; i < n_plans; ++i) {
         if (!plans[i]) return FIRM_EINVAL;
         if (plans[i]->P.p.W != plans[0]->P.p.W) return FIRM_EINVAL;
+        if (plans[i]->P.p.flags & FIRM_FLAG_FP64_CG) return FIRM_EINVAL;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return FIRM_EINVAL;
     }

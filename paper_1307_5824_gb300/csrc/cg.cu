@@ -160,13 +160,11 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(float* __restrict__ x,
     }
 }
 
-// Enough blocks that each thread updates one float4 (all its loads in flight at once),
-// at least four per SM, at most the reduction's slot count.
+// Four blocks per SM: enough loads in flight, and few enough blocks that the
+// last-block ticket (one atomic per block on one address) stays cheap.
 static int cg_blocks(const Plan& P) {
-    const long long n4 = (long long)P.N * P.N * P.N / 4;
-    long long b = (n4 + kCgThreads - 1) / kCgThreads;
-    if (b < P.num_sms * 4) b = P.num_sms * 4;
-    return (int)(b < kRedSlots ? b : kRedSlots);
+    const int b = P.num_sms * 4;
+    return b < kRedSlots ? b : kRedSlots;
 }
 
 cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_tol, bool use_pc) {

@@ -105,6 +105,14 @@ struct Workspace {
     double* hist = nullptr;
     CgState* cg = nullptr;
     float* lam = nullptr;           // device: [0] lam_eff, [1] Ker(0) of the last kernel
+    // FP64 CG mode only (FIRM_FLAG_FP64_CG; empty otherwise)
+    double2* tw64 = nullptr;        // exp(-2 pi i k / 2N), k < N
+    double* khat64 = nullptr;       // Re K-hat, full (2N)^3
+    double2* c64 = nullptr;         // (2N)^3 FFT buffer
+    double* x64 = nullptr;
+    double* r64 = nullptr;
+    double* p64 = nullptr;
+    double* q64 = nullptr;
     size_t total = 0;
 };
 
@@ -190,6 +198,12 @@ cudaError_t launch_view_axis(Plan& P, const double* R, int M);
 cudaError_t launch_pc_features(Plan& P, int M, float* hist);
 cudaError_t launch_pc_target_sums(Plan& P, double* s1, double* s2);
 cudaError_t launch_pc_from_table(Plan& P, const float* table);
+
+// ---- launchers (cg64.cu): the FP64 CG mode ----
+cudaError_t launch_khat64(Plan& P);                 // khat64 from the Ker half box
+// CG from x0 = 0 (first_iter == 0 queues the initialisation), then n_iter iterations.
+cudaError_t launch_cg64(Plan& P, const float* rhs, int max_iter, double rel_tol, int first_iter, int n_iter);
+cudaError_t launch_cg64_result(Plan& P);            // x64 -> ws.x (float)
 
 // ---- launchers (cg.cu) ----
 cudaError_t launch_cg_init(Plan& P, const float* rhs, int max_iter, double rel_tol, bool use_pc);

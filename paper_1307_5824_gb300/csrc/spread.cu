@@ -9,12 +9,13 @@
 //
 // Pipeline per channel (kernel: weights h^2 on G = 4N; right-hand side: weights
 // h b on G = 2N):
-//   1. bin:    count points per 16^3 brick (warp-aggregated atomics), scan, and
-//              scatter point ids into per-brick segments; cut segments into work
-//              items of at most kChunk points.
-//   2. spread: persistent CTAs take work items; each accumulates its points into a
-//              (16 + W)^3 shared-memory region with shared atomics (FP32), then adds
-//              the region into the FP64 global grid with FP64 atomics.
+//   1. bin:    count points per 8^3 brick (warp-aggregated atomics), scan, scatter
+//              point ids into per-brick segments cut into work items of at most
+//              `chunk` points, and order each item round-robin over bank classes.
+//   2. spread: persistent CTAs take work items; each accumulates its points into an
+//              (8 + W)^3 shared-memory region in int32 fixed point (native shared
+//              atomics), folds it into FP32 every 512 or 1024 points, then adds the region
+//              into the FP64 global grid with FP64 atomics.
 #include <cuda_runtime.h>
 
 #include "firm_internal.h"
@@ -54,18 +55,25 @@ cudaError_t launch_geom(const double* R, int M, ImgGeom* geom, cudaStream_t s) {
 __device__ __forceinline__ void cell_coord(float sk1, float sk2, float uh, float ul, float vh, float vl,
                                            int halfG, int G, int& I, float& f) {
     // explicit rounding intrinsics: no contraction, so every kernel that calls this
-    // (binning and spreading) gets bit-identical cells
+    // (binning and spreading) gets bit-identical cells.  Round-to-nearest integers by
+    // adding 1.5 * 2^23 (|a|, |b| <= G/2 < 2^22); the bit pattern then holds the integer.
+    constexpr float kMagic = 12582912.0f;
+    constexpr int kMagicBits = 0x4B400000;
     const float a = __fmul_rn(sk1, uh), ea = fmaf(sk1, uh, -a);
     const float b = __fmul_rn(sk2, vh), eb = fmaf(sk2, vh, -b);
-    const float ra = rintf(a), rb = rintf(b);
+    const float ma = __fadd_rn(a, kMagic), mb = __fadd_rn(b, kMagic);
+    const float ra = __fsub_rn(ma, kMagic), rb = __fsub_rn(mb, kMagic);
     const float lo = __fadd_rn(__fadd_rn(ea, eb), fmaf(sk1, ul, __fmul_rn(sk2, vl)));
     const float fr = __fadd_rn(__fadd_rn(__fsub_rn(a, ra), __fsub_rn(b, rb)), lo);
     const float fl = floorf(fr);
     float ff = __fsub_rn(fr, fl);
-    int ii = (int)ra + (int)rb + (int)fl + halfG;
+    int ii = (__float_as_int(ma) - kMagicBits) + (__float_as_int(mb) - kMagicBits) +
+             (__float_as_int(__fadd_rn(fl, kMagic)) - kMagicBits) + halfG;
     if (ff >= 1.0f) { ff = 0.0f; ii += 1; }
-    ii %= G;
-    if (ii < 0) ii += G;
+    // |k1 u + k2 v| <= |k| <= N/2 (u, v: parts of a unit column of R), so ii lies in
+    // [-1, G + 1]: one wrap either way is the periodic index
+    if (ii >= G) ii -= G;
+    else if (ii < 0) ii += G;
     I = ii;
     f = ff;
 }
@@ -383,9 +391,10 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
 //
 // Level 1: int32 fixed point in shared memory, one native shared-memory atomic add
 // per tap (v * S rounded to nearest through the FMA with 1.5 * 2^23).  S is a power
-// of two with max|w| * S <= 2^21, and level 1 is folded into the FP32 level-2 region
-// after every 512 points of the block (two per thread), so a cell can never exceed
-// 2^30.  Level 2 is added into the FP64 grid when the work item ends.
+// of two with max|w| * S <= 2^21 (A*b) or 2^20 (kernel), and level 1 is folded into
+// the FP32 level-2 region after every 512 (A*b) or 1024 (kernel) points of the block,
+// so a cell can never exceed 2^30.  Level 2 is added into the FP64 grid when the work
+// item ends.
 // ---------------------------------------------------------------------------
 struct SpreadArgs {
     const uint32_t* payload;
@@ -411,6 +420,14 @@ __device__ __forceinline__ float2 point_weight(const SpreadArgs& a, bool cplx, i
     const int g = min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1);
     return make_float2(__ldg(&a.h2[(size_t)g * a.nH + t]), 0.0f);
 }
+
+// Points each thread spreads between two folds of level 1 into level 2.  A fold is a
+// block-wide barrier; with PPR points per thread a cell can receive at most 256 * PPR
+// taps between folds, so a tap is scaled to at most 2^30 / (256 * PPR): 2^21 for the
+// A*b channel (PPR 2) and 2^20 for the kernel channel (PPR 4, half the barriers; the
+// extra bit of rounding takes Ker's fixed-point error from ~6e-7 to ~1.2e-6, still
+// well below the window's own ~5e-6 at W=6).
+template <bool CPLX> struct SpreadRound { static constexpr int PPR = CPLX ? 2 : 4; static constexpr int kScaleBits = CPLX ? 21 : 20; };
 
 // One work item (a piece of one brick's points) into the brick's shared-memory region,
 // then the region into the FP64 grid.  lev1/lev2 are zero on entry and on return.
@@ -445,14 +462,15 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
 #pragma unroll
         for (int i = 1; i < kSpreadWarps; ++i) wmax = fmaxf(wmax, s_red[i]);
     }
-    const int rounds = (((wk.z + kSpreadThreads - 1) / kSpreadThreads) + 1) / 2;
+    constexpr int PPR = SpreadRound<CPLX>::PPR, SB = SpreadRound<CPLX>::kScaleBits;
+    const int rounds = (((wk.z + kSpreadThreads - 1) / kSpreadThreads) + PPR - 1) / PPR;
     int ex = 0;
     if (wmax > 0.0f) frexpf(wmax, &ex);                // wmax <= 2^ex
-    const float S = ldexpf(1.0f, 21 - ex), invS = ldexpf(1.0f, ex - 21);
+    const float S = ldexpf(1.0f, SB - ex), invS = ldexpf(1.0f, ex - SB);
     for (int r = 0; r < rounds; ++r) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int i = 2 * r + q;
+#pragma unroll 2
+        for (int q = 0; q < PPR; ++q) {
+            const int i = PPR * r + q;
             if (i >= my_n) continue;
             const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
             const int m = (int)(id >> kTBits);

@@ -13,12 +13,12 @@ class Reconstructor:
 
     def __init__(self, N: int, M: int, groups=None, W: int = 6, lam: float = 0.0,
                  lambda_mode: int = L.FIRM_LAMBDA_RELATIVE, img_dtype: int = L.FIRM_IMG_F32,
-                 device="cuda:0", stream=None):
+                 device="cuda:0", stream=None, flags: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("the FIRM CUDA path needs a CUDA device")
         self.device = torch.device(device)
         table = np.zeros((0, 6)) if groups is None else np.asarray(groups, float).reshape(-1, 6)
-        self.params = L.make_params(N, M, table.shape[0], W, 2.0, lam, lambda_mode, 0, img_dtype, 0)
+        self.params = L.make_params(N, M, table.shape[0], W, 2.0, lam, lambda_mode, 0, img_dtype, flags)
         self._groups = L.make_groups(table)
         self.ws_bytes = L.firm_workspace_size(self.params)
         with torch.cuda.device(self.device):

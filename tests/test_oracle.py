@@ -563,3 +563,44 @@ def test_cg_trajectory_horizon_under_tiny_operator_noise():
         xb, _, _ = O.cg(noisy, rhs, it)
         dev[it] = np.linalg.norm(xb - xa) / np.linalg.norm(xa)
     assert dev[10] < 1e-6 and dev[25] > 1e-3, dev
+
+
+def test_c1_fp32_fft_drift():
+    """The N=32 workload's 10 CG iterations (lambda = 0) with the circulant apply done by a
+    library FFT in FP32 (complex64) and FP32 CG vectors, everything else as the oracle:
+    the iterate moves by ~8e-5 from the FP64 one (while white noise of the same size,
+    1e-7 per apply, moves it by only ~3e-6).  This is the floor of any FP32-FFT path on
+    this workload and the basis of its FP32 gates."""
+    sf = pytest.importorskip("scipy.fft")
+    inp = synth.config_inputs("C1")
+    N = inp["N"]
+    K = O.disc(N)
+    h = np.ones((inp["M"], K.shape[0]))
+    Ker = O.kernel(inp["R"], h, K, N).real
+    rhs = O.backproject(inp["images"].astype(np.float64), inp["shifts"], inp["R"], h, K)
+    Kh = O.khat(Ker).real
+    Kh32 = Kh.astype(np.float32)
+
+    def op32(v):
+        P = np.zeros((2 * N,) * 3, np.complex64)
+        P[:N, :N, :N] = v.astype(np.float32)
+        Fv = sf.fftn(P)
+        Fv *= Kh32
+        return sf.ifftn(Fv)[:N, :N, :N].real.astype(np.float64)
+
+    f32 = lambda v: v.astype(np.float32).astype(np.float64)
+    x = np.zeros(rhs.shape)
+    r = rhs.copy()
+    p = f32(rhs)
+    rr = float((r * r).sum())
+    for _ in range(10):
+        q = f32(op32(p))
+        a = rr / float((p * q).sum())
+        x = f32(x + a * p)
+        r = r - a * q
+        rr2 = float((r * r).sum())
+        p = f32(rr2 / rr * p + r)
+        rr = rr2
+    xo, _, _ = O.cg(lambda v: O.toeplitz_apply(Kh, v).real, rhs, 10)
+    drift = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    assert 2e-5 <= drift <= 3e-4, drift
