@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--precond", default="learned", choices=["none", "circulant", "binned", "learned"])
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-CG comparison run")
     ap.add_argument("--train-kernels", type=int, default=2000, help="N=64 kernels the learned preconditioner trains on")
+    ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned preconditioner")
+    ap.add_argument("--train-m-max", type=int, default=3000, help="largest image count of a training kernel")
+    ap.add_argument("--train-lr-final", type=float, default=None, help="final Adam step size (cosine decay from 1e-3)")
     ap.add_argument("--workload", default="C3", choices=["C3", "C5", "C4"],
                     help="C3: 50k Haar views, 20 groups; C5: 40k views 85%% in a 15 degree cap, 8 groups; "
                          "C4: 64 independent reconstructions, N in {48,64,80,96}, 1k-8k images, 25 CG iterations")
@@ -370,10 +373,11 @@ def main():
     if args.precond == "learned":
         from paper_1307_5824_gb300 import learned
         t0 = time.perf_counter()
-        X, T = learned.generate(args.train_kernels, N=64, device=dev)
+        X, T = learned.generate(args.train_kernels, N=64, m_range=(500, args.train_m_max), device=dev)
         t_gen = time.perf_counter() - t0
-        net, hist = learned.train(X[: int(0.9 * len(X))], T[: int(0.9 * len(X))], device=dev)
-        train_info = {"kernels": int(len(X)), "gen_s": round(t_gen, 1), "loss": hist,
+        net, hist = learned.train(X[: int(0.9 * len(X))], T[: int(0.9 * len(X))], steps=args.train_steps,
+                                  lr_final=args.train_lr_final, device=dev)
+        train_info = {"kernels": int(len(X)), "steps": args.train_steps, "gen_s": round(t_gen, 1), "loss": hist,
                       "val_mse_bf16": learned.evaluate(net, X[int(0.9 * len(X)):], T[int(0.9 * len(X)):], bf16=True)}
     else:
         rec.set_precond(pc_modes[args.precond])

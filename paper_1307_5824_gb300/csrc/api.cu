@@ -174,12 +174,18 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     // union: staged images | point ids | FFT intermediates (never live together)
     const size_t fx1 = std::max({Gk * Gk * (N + 1), Gr * Gr * N, H3});
     const size_t fx2 = std::max({Gk * 2 * N * (N + 1), Gr * N * N, H3});
-    const size_t pay_bytes = ((M * nH * sizeof(uint32_t) + 255) & ~(size_t)255) + M * nH;
+    // point ids, bank bytes, the A*b weights in scatter order and the sort's permutation
+    const size_t ids_bytes = (M * nH * sizeof(uint32_t) + 255) & ~(size_t)255;
+    const size_t cls_bytes = (M * nH + 255) & ~(size_t)255;
+    const size_t smp_bytes = (M * nH * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t pay_bytes = ids_bytes + cls_bytes + smp_bytes + M * nH * sizeof(uint16_t);
     const size_t u_bytes = std::max({M * N * N * esz, pay_bytes, (fx1 + fx2) * sizeof(float2) + 256});
     char* u = c.take<char>(u_bytes);
     w.images = u;
     w.payload = reinterpret_cast<uint32_t*>(u);
-    w.cls = u ? reinterpret_cast<uint8_t*>(u + ((M * nH * sizeof(uint32_t) + 255) & ~(size_t)255)) : nullptr;
+    w.cls = u ? reinterpret_cast<uint8_t*>(u + ids_bytes) : nullptr;
+    w.samples_b = u ? reinterpret_cast<float2*>(u + ids_bytes + cls_bytes) : nullptr;
+    w.perm = u ? reinterpret_cast<uint16_t*>(u + ids_bytes + cls_bytes + smp_bytes) : nullptr;
     w.fx1 = reinterpret_cast<float2*>(u);
     w.fx2 = u ? reinterpret_cast<float2*>(u + ((fx1 * sizeof(float2) + 255) & ~(size_t)255)) : nullptr;
     w.ker = c.take<float>(H3);

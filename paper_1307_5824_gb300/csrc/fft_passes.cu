@@ -301,9 +301,11 @@ __device__ __forceinline__ float img_val(const void* p, size_t i) {
 }
 
 template <int N> __host__ __device__ constexpr int img_rows() { return kThreads / Split<N>::L2; }
+// the N/2 + 1 columns of the half spectrum in two tiles (every thread busy in step 1)
+template <int N> __host__ __device__ constexpr int img_col_tile() { return (N / 2 + 2) / 2; }
 template <int N> __host__ __device__ constexpr int img_smem_elems() {
     constexpr int a = smem_elems<N, false>(img_rows<N>());
-    constexpr int b = smem_elems<N, true>(kTX);
+    constexpr int b = smem_elems<N, true>(img_col_tile<N>());
     return N * (N / 2 + 1) + (a > b ? a : b);
 }
 
@@ -322,8 +324,9 @@ __global__ void __launch_bounds__(kThreads) k_image_dft(const ImgArgs a) {
         auto st = [&](int line, int k, float2 v) { if (k <= N / 2) S1[(r0 + line) * H1 + k] = v; };
         block_fft<N, -1, false>(nl, ld, st, scr, a.tw);
     }
-    for (int c0 = 0; c0 < H1; c0 += kTX) {
-        const int nl = min(kTX, H1 - c0);
+    constexpr int CT = img_col_tile<N>();
+    for (int c0 = 0; c0 < H1; c0 += CT) {
+        const int nl = min(CT, H1 - c0);
         auto ld = [&](int line, int n) { return S1[n * H1 + c0 + line]; };
         auto st = [&](int line, int k, float2 v) { S1[k * H1 + c0 + line] = v; };
         block_fft<N, -1, true>(nl, ld, st, scr, a.tw);

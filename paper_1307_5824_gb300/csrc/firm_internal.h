@@ -78,6 +78,8 @@ struct Workspace {
     uint32_t* cursor = nullptr;
     uint32_t* payload = nullptr;    // point ids m * nH + t sorted by brick, then bank class
     uint8_t* cls = nullptr;         // bank class of each binned point
+    float2* samples_b = nullptr;    // A*b weights in scatter order (written by the scatter pass)
+    uint16_t* perm = nullptr;       // per payload position: index in scatter order within its piece
     int4* work = nullptr;           // (brick, start, count, -)
     int* counters = nullptr;        // [0] work items, [1] work cursor, [2] error flag
     double* grid = nullptr;         // fine grid, FP64 (real for Ker, complex for A*b)

@@ -143,6 +143,8 @@ struct BinArgs {
     uint32_t* count;       // count pass: per-brick counters; scatter pass: cursors
     uint32_t* payload;     // scatter pass output: point ids m * nH + t
     uint8_t* cls;          // scatter pass output: bank class of each point
+    const float2* samples; // A*b channel: weights [m][t], copied to samples_b[slot] by the scatter
+    float2* samples_b;     //   (consecutive lanes read consecutive t: coalesced)
     long long npts;        // M * nH
     int nH, G, halfG, nb;  // nb = bricks per axis
     float scale;
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a, int M) {
                 const uint32_t slot = base + (uint32_t)(lane - my_head);
                 a.payload[slot] = ((uint32_t)m << kTBits) | (uint32_t)t;
                 a.cls[slot] = (uint8_t)c;
+                if (a.samples) a.samples_b[slot] = __ldg(&a.samples[(size_t)m * a.nH + t]);
             }
         }
     }
@@ -255,8 +258,13 @@ __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__
 // correct, this one just conflicts more.
 constexpr int kSortLevels = 1024;
 constexpr int kSortSmem = kChunk * (4 + 1) + kSortLevels * (4 + 4);   // ids, classes, masks, prefix
+// With perm != nullptr (A*b channel) the piece's pre-sort index of each point is kept
+// in perm at its new position: the A*b weights stay where the scatter put them (in
+// scatter order, samples_b), and the spreading pass reads them through perm from
+// within the piece's own 64 KB window instead of one scattered sector per point.
 __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ payload, const uint8_t* __restrict__ cls,
-                                                    const int4* __restrict__ work, const int* __restrict__ counters) {
+                                                    const int4* __restrict__ work, const int* __restrict__ counters,
+                                                    uint16_t* __restrict__ perm) {
     extern __shared__ uint32_t sm_u[];
     uint32_t* s_ids = sm_u;                                         // kChunk
     uint32_t* s_mask = s_ids + kChunk;                              // kSortLevels: classes with n_c > r
@@ -330,13 +338,14 @@ __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ paylo
                 pos = s_pre[r] + __popc(s_mask[r] & ((1u << c) - 1u));
             }
             payload[wk.y + pos] = s_ids[i];
+            if (perm) perm[wk.y + pos] = (uint16_t)i;
         }
         __syncthreads();
     }
 }
 
 template <int W>
-static void bin_w(Plan& P, const BinArgs& a0, int nbricks) {
+static void bin_w(Plan& P, const BinArgs& a0, int nbricks, bool kc) {
     Workspace& w = P.ws;
     BinArgs a = a0;
     const int M = (int)(a.npts / a.nH);
@@ -347,7 +356,8 @@ static void bin_w(Plan& P, const BinArgs& a0, int nbricks) {
     a.count = w.cursor;
     k_bin<W, true><<<grid, 256, 0, P.stream>>>(a, M);
     cudaFuncSetAttribute(k_class_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
-    k_class_sort<<<P.num_sms * 4, 256, kSortSmem, P.stream>>>(w.payload, w.cls, w.work, w.counters);
+    k_class_sort<<<P.num_sms * 4, 256, kSortSmem, P.stream>>>(w.payload, w.cls, w.work, w.counters,
+                                                               kc ? nullptr : w.perm);
 }
 
 cudaError_t launch_bin(Plan& P, int M, bool kc) {
@@ -363,6 +373,8 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
     a.count = w.count;
     a.payload = w.payload;
     a.cls = w.cls;
+    a.samples = kc ? nullptr : w.samples;
+    a.samples_b = w.samples_b;
     a.npts = (long long)M * P.nH;
     a.nH = P.nH;
     a.G = G;
@@ -377,9 +389,9 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
         return cudaGetLastError();
     }
     switch (P.p.W) {
-        case 6: bin_w<6>(P, a, nbricks); break;
-        case 7: bin_w<7>(P, a, nbricks); break;
-        case 8: bin_w<8>(P, a, nbricks); break;
+        case 6: bin_w<6>(P, a, nbricks, kc); break;
+        case 7: bin_w<7>(P, a, nbricks, kc); break;
+        case 8: bin_w<8>(P, a, nbricks, kc); break;
         default: return cudaErrorInvalidValue;
     }
     P.launches += 4;
@@ -404,7 +416,8 @@ struct SpreadArgs {
     const int32_t* htab;
     const int32_t* gid;
     const float* h2;          // kernel channel weights [group][t]
-    const float2* samples;    // right-hand-side weights [m][t]
+    const float2* samples_b;  // right-hand-side weights in scatter order
+    const uint16_t* perm;     // per payload position: the point's index in scatter order
     double* grid;             // G^3 real, or G^3 complex interleaved (re, im)
     int G, halfG, nb, nH, n_ctf;
     float scale;
@@ -415,8 +428,11 @@ struct SpreadArgs {
 constexpr int kSpreadThreads = 256;
 constexpr int kSpreadWarps = kSpreadThreads / 32;
 
-__device__ __forceinline__ float2 point_weight(const SpreadArgs& a, bool cplx, int m, int t) {
-    if (cplx) return __ldg(&a.samples[(size_t)m * a.nH + t]);
+// Weight of the point at payload position pos (image m, sample t) of the piece
+// starting at p0.
+__device__ __forceinline__ float2 point_weight(const SpreadArgs& a, bool cplx, int m, int t, uint32_t p0,
+                                               uint32_t pos) {
+    if (cplx) return __ldg(&a.samples_b[p0 + __ldg(&a.perm[pos])]);
     const int g = min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1);
     return make_float2(__ldg(&a.h2[(size_t)g * a.nH + t]), 0.0f);
 }
@@ -451,7 +467,8 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
     if (wmax <= 0.0f) {
         for (int i = 0; i < my_n; ++i) {
             const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
-            const float2 wv = point_weight(a, CPLX, (int)(id >> kTBits), (int)(id & ((1u << kTBits) - 1u)));
+            const float2 wv = point_weight(a, CPLX, (int)(id >> kTBits), (int)(id & ((1u << kTBits) - 1u)),
+                                           (uint32_t)wk.y, s0 + kSpreadThreads * i);
             wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
         }
 #pragma unroll
@@ -481,7 +498,7 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
                 atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
                 continue;
             }
-            const float2 wv = point_weight(a, CPLX, m, t);
+            const float2 wv = point_weight(a, CPLX, m, t, (uint32_t)wk.y, s0 + kSpreadThreads * i);
             float wx[W], wy[W], wz[W];
             window_taps<W>(poly, p.f[0], wx);
             window_taps<W>(poly, p.f[1], wy);
@@ -664,7 +681,8 @@ static SpreadArgs spread_args(Plan& P, bool kc) {
     a.htab = w.htab;
     a.gid = P.cur_gid;
     a.h2 = w.h2;
-    a.samples = w.samples;
+    a.samples_b = w.samples_b;
+    a.perm = w.perm;
     a.grid = w.grid;
     a.G = G;
     a.halfG = G / 2;

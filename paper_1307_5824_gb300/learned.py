@@ -82,8 +82,10 @@ def init_params(seed: int = 52) -> np.ndarray:
 
 
 def train(X: np.ndarray, T: np.ndarray, steps: int = 3000, batch: int = 64, lr: float = 1e-3, seed: int = 53,
-          device="cuda:0", log_every: int = 500):
-    """Adam on the mean squared error; returns (params on the device, loss history)."""
+          device="cuda:0", log_every: int = 500, lr_final: float | None = None):
+    """Adam on the mean squared error, the step size decayed from lr to lr_final on a
+    half cosine (constant when lr_final is None); returns (params on the device, loss
+    history)."""
     dev = torch.device(device)
     rng = np.random.default_rng(seed)
     params = torch.from_numpy(init_params(seed - 1)).to(dev)
@@ -101,7 +103,8 @@ def train(X: np.ndarray, T: np.ndarray, steps: int = 3000, batch: int = 64, lr: 
         xb = Xd.index_select(0, idx).contiguous()
         tb = Td.index_select(0, idx).contiguous()
         L.firm_mlp_grad(params, batch, xb, tb, g, work, loss, s)
-        L.firm_mlp_adam(params, g, m, v, step, lr, s)
+        lr_t = lr if lr_final is None else lr_final + (lr - lr_final) * 0.5 * (1.0 + np.cos(np.pi * (step - 1) / steps))
+        L.firm_mlp_adam(params, g, m, v, step, lr_t, s)
         if step % log_every == 0 or step == 1:
             hist.append((step, float(loss.item())))
     return params, hist

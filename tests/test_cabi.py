@@ -32,7 +32,14 @@ def test_workspace_size_and_argument_checks(lib):
     p = L.make_params(32, 200, 0, 6)
     small = L.firm_workspace_size(p)
     big = L.firm_workspace_size(L.make_params(128, 50000, 20, 7, img_dtype=L.FIRM_IMG_BF16))
-    assert 0 < small < big < 8 * 2 ** 30
+    # N=128, 50k images: 4.1 GB of binned points (ids, bank bytes, A*b weights in scatter
+    # order, the sort's permutation), the 1.07 GB fine grid, K-hat, CG vectors: < 10 GiB
+    assert 0 < small < big < 10 * 2 ** 30
+    # the FP64 CG mode adds its (2N)^3 buffers only when asked for (N <= 64)
+    p64 = L.make_params(32, 200, 0, 6, flags=L.FIRM_FLAG_FP64_CG)
+    assert L.firm_workspace_size(p64) > small
+    with pytest.raises(L.FirmError):
+        L.firm_workspace_size(L.make_params(128, 10, 0, 6, flags=L.FIRM_FLAG_FP64_CG))
     for bad in (L.make_params(30, 10), L.make_params(32, 10, W=5), L.make_params(32, 10, sigma=1.5),
                 L.make_params(32, 10, disc_mode=1), L.make_params(32, -1)):
         with pytest.raises(L.FirmError) as e:
