@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--train-kernels", type=int, default=2000, help="N=64 kernels the learned preconditioner trains on")
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned preconditioner")
     ap.add_argument("--train-m-max", type=int, default=3000, help="largest image count of a training kernel")
+    ap.add_argument("--train-groups", type=int, default=4,
+                    help="training kernels use 1..this many of the defocus values (max 20)")
+    ap.add_argument("--train-defocus", type=int, default=8, help="defocus values (1.0-3.5 um) training draws from")
     ap.add_argument("--train-lr-final", type=float, default=None, help="final Adam step size (cosine decay from 1e-3)")
     ap.add_argument("--workload", default="C3", choices=["C3", "C5", "C4"],
                     help="C3: 50k Haar views, 20 groups; C5: 40k views 85%% in a 15 degree cap, 8 groups; "
@@ -373,7 +376,8 @@ def main():
     if args.precond == "learned":
         from paper_1307_5824_gb300 import learned
         t0 = time.perf_counter()
-        X, T = learned.generate(args.train_kernels, N=64, m_range=(500, args.train_m_max), device=dev)
+        X, T = learned.generate(args.train_kernels, N=64, m_range=(500, args.train_m_max), device=dev,
+                                defocus_um=np.linspace(1.0, 3.5, args.train_defocus), max_groups=args.train_groups)
         t_gen = time.perf_counter() - t0
         net, hist = learned.train(X[: int(0.9 * len(X))], T[: int(0.9 * len(X))], steps=args.train_steps,
                                   lr_final=args.train_lr_final, device=dev)
@@ -488,13 +492,42 @@ def main():
     atoms = M * nH * W ** 3 * (2 if dom == "spread_rhs" else 1)
     peak = 152 * 32 * 2.07e9
     achieved = atoms / (stages[dom] * 1e-3)
+    kname = f"k_spread<{W},{'complex' if dom == 'spread_rhs' else 'real'}>"
     traffic = None
     prof = os.path.join(ROOT, "profiles", "spread_traffic.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and (N, M, W) == (128, 50000, 6):   # the figure is for this workload
         try:
-            traffic = json.load(open(prof)).get(dom)
+            traffic = json.load(open(prof)).get(kname)
         except Exception:
             traffic = None
+    hbm_peak = None
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        hbm_src = "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        hbm_peak, hbm_src = 6800.0, "fallback"
+    # a7 alone: Toeplitz applies on device buffers, CUDA events on the plan's stream.
+    # Algorithmic bytes of one apply (five passes): x rows in + t1 out, t1 -> t2 (y),
+    # t2 + K-hat -> t2 (z), t2 -> t1 (y inverse), t1 + x -> y.
+    H = N * N * (N + 1) * 8
+    toep_bytes = (N ** 3 * 4 + H) + (H + 2 * H) + (2 * H + 2 * N * 2 * N * (N + 1) * 4 + 2 * H) + (2 * H + H) \
+        + (H + 2 * N ** 3 * 4)
+    xa = torch.randn((N, N, N), device=dev)
+    ya = torch.empty_like(xa)
+    for _ in range(3):
+        rec.toeplitz_apply(xa, ya)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_app = 50
+    torch.cuda.synchronize(dev)
+    t0e.record(stream)
+    for _ in range(n_app):
+        rec.toeplitz_apply(xa, ya)
+    t1e.record(stream)
+    torch.cuda.synchronize(dev)
+    toep_s = t0e.elapsed_time(t1e) / 1e3 / n_app
+    toeplitz = {"applies_per_s": 1.0 / toep_s, "us_per_apply": toep_s * 1e6, "algorithmic_bytes": toep_bytes,
+                "achieved_gbs": toep_bytes / toep_s / 1e9, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": toep_bytes / toep_s / 1e9 / hbm_peak, "peak_source": hbm_src}
 
     cpu = None
     if not args.no_cpu:
@@ -513,11 +546,15 @@ def main():
                    "l2": "inputs larger than L2: 1.64 GB BF16 images read and a 1.07 GB FP64 fine grid "
                          "written every step"},
         "spread_gpts_per_s": pts / (spread_ms * 1e-3) / 1e9,
+        "spread_gpts_per_s_by_channel": {"kernel": pts / (stages["spread_ker"] * 1e-3) / 1e9,
+                                         "rhs": pts / (stages["spread_rhs"] * 1e-3) / 1e9},
         "spread_points": pts,
-        "toeplitz_applies_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
+        "toeplitz_applies_per_s": toeplitz["applies_per_s"],
+        "toeplitz": toeplitz,
+        "cg_iters_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
         "cg_iters": iters,
         "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},
-        "roofline": {"kernel": f"k_spread<{W},{'complex' if dom == 'spread_rhs' else 'real'}>", "bound": "alu",
+        "roofline": {"kernel": kname, "bound": "alu",
                      "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tatomic/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "derived: 152 SMs x 32 shared-atomic lanes/clk x 2.07 GHz"},

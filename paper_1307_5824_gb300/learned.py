@@ -45,10 +45,13 @@ def net_input(feat: np.ndarray) -> np.ndarray:
     return np.log(NBINS * np.asarray(feat, np.float64) + 1e-3).astype(np.float32)
 
 
-def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3000), device="cuda:0"):
-    """(X, T): network inputs and targets of n_kernels method-generated kernels."""
+def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3000), device="cuda:0",
+             defocus_um=DEFOCUS_UM, max_groups: int = 4):
+    """(X, T): network inputs and targets of n_kernels method-generated kernels; each
+    kernel uses 1..max_groups of the defocus values."""
     rng = np.random.default_rng(seed)
-    groups = synth.ctf_group_table(DEFOCUS_UM)
+    defocus_um = np.asarray(defocus_um, float)
+    groups = synth.ctf_group_table(defocus_um)
     rec = Reconstructor(N, m_range[1], groups=groups, W=6, lam=1e-3, device=device)
     X = np.empty((n_kernels, NBINS), np.float32)
     T = np.empty((n_kernels, NBINS), np.float32)
@@ -57,7 +60,7 @@ def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3
     for i in range(n_kernels):
         M = int(rng.integers(m_range[0], m_range[1] + 1))
         R = random_rotations(M, rng)
-        sub = rng.choice(len(DEFOCUS_UM), int(rng.integers(1, 5)), replace=False)
+        sub = rng.choice(len(defocus_um), int(rng.integers(1, min(max_groups, len(defocus_um)) + 1)), replace=False)
         gid = sub[rng.integers(0, len(sub), M)].astype(np.int32)
         rec.kernel(np.ascontiguousarray(R.reshape(M, 9)), gid, M=M)
         rec.pc_features(f)
