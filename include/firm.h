@@ -229,8 +229,25 @@ int firm_lambda_eff(firm_plan_t plan, double* out);
  *                  k = 0 sample halved (the symmetric completion doubles it back).
  *                  |H| = (|K| + 1) / 2, ordered by k1 = 0..N/2 then k2 ascending,
  *                  starting (0,0), (0,1), ... (0,N/2), (1,-..), ... */
-enum { FIRM_OUT_KER = 0, FIRM_OUT_KHAT = 1, FIRM_OUT_RHS = 2, FIRM_OUT_SAMPLES = 3 };
+enum { FIRM_OUT_KER = 0, FIRM_OUT_KHAT = 1, FIRM_OUT_RHS = 2, FIRM_OUT_SAMPLES = 3,
+       FIRM_OUT_BIN_IDS = 4, FIRM_OUT_BIN_WORK = 5 };
 int firm_copy_out(firm_plan_t plan, int which, void* dst);
+
+/* The binning step of the spreading (slice geometry of eq. forward-projector, points
+ * grouped per brick of the fine grid; Section 3.4 steps 2-3) run alone, for
+ * verification: the points of images 0..M-1 (R: M x 9 float64) are binned for the
+ * kernel channel (channel 0: fine grid 4N, bricks of 8^3 cells) or the A*b channel
+ * (channel 1: fine grid 2N).  Afterwards
+ *   FIRM_OUT_BIN_IDS   M * |H| uint32 point ids (m << 13 | t, t the half-disc index of
+ *                      FIRM_OUT_SAMPLES), grouped by work item;
+ *   FIRM_OUT_BIN_WORK  n_work work items, 4 int32 each: (brick, first id position,
+ *                      point count, 0); brick = (bz * nb + by) * nb + bx;
+ * and firm_bin_info gives n_work, M * |H|, nb (bricks per axis) and the most points of
+ * an item.  Within an item the points are ordered round-robin over the 32 bank
+ * classes of their first tap.  firm_bin reuses the memory of the kernel and A*b
+ * results: call firm_kernel / firm_backproject again before using those. */
+int firm_bin(firm_plan_t plan, int M, const double* R, int channel);
+int firm_bin_info(firm_plan_t plan, int* n_work, int* n_points, int* bricks_per_axis, int* chunk);
 
 /* Device time of the last call of each stage, in milliseconds between CUDA events
  * recorded on the plan's stream around the stage (recorded only while timing is on,

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libfirm.so")
 FIRM_OK, FIRM_EINVAL, FIRM_ENOMEM, FIRM_ECUDA, FIRM_ENOTCONV, FIRM_EBREAKDOWN, FIRM_ETIMEOUT, FIRM_ESTATE = range(8)
 FIRM_IMG_F32, FIRM_IMG_BF16 = 0, 1
 FIRM_LAMBDA_RELATIVE, FIRM_LAMBDA_ABSOLUTE = 0, 1
-FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES = 0, 1, 2, 3
+FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES, FIRM_OUT_BIN_IDS, FIRM_OUT_BIN_WORK = 0, 1, 2, 3, 4, 5
 FIRM_PRECOND_NONE, FIRM_PRECOND_CIRCULANT, FIRM_PRECOND_BINNED, FIRM_PRECOND_TABLE = 0, 1, 2, 3
 FIRM_BATCH_GRAPH, FIRM_BATCH_PERSISTENT = 1, 2
 FIRM_FLAG_FP64_CG = 1
@@ -28,6 +28,7 @@ EXPORTED = [
     "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_target", "firm_pc_axis",
     "firm_set_precond_table", "firm_mlp_forward", "firm_mlp_to_bf16", "firm_mlp_forward_bf16", "firm_mlp_grad",
     "firm_mlp_adam", "firm_mlp_param_count", "firm_mlp_work_floats",
+    "firm_bin", "firm_bin_info",
     "firm_batch_workspace_size", "firm_batch_create", "firm_batch_run", "firm_batch_wait", "firm_batch_set_config",
     "firm_batch_get_config", "firm_batch_tune", "firm_batch_launch_count", "firm_batch_destroy",
     "firm_destroy", "firm_strerror",
@@ -93,6 +94,8 @@ def lib() -> ctypes.CDLL:
     L.firm_mlp_param_count.argtypes = []
     L.firm_mlp_work_floats.argtypes = [i]
     L.firm_mlp_work_floats.restype = ctypes.c_size_t
+    L.firm_bin.argtypes = [vp, i, vp, i]
+    L.firm_bin_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.firm_batch_workspace_size.argtypes = [i, ctypes.POINTER(ctypes.c_size_t)]
     L.firm_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), i, vp, ctypes.c_size_t, vp]
     L.firm_batch_run.argtypes = [vp, ctypes.POINTER(firm_batch_item), i, i]
@@ -351,3 +354,14 @@ def firm_batch_launch_count(batch) -> int:
 def firm_batch_destroy(batch):
     if batch:
         lib().firm_batch_destroy(batch)
+
+
+def firm_bin(plan, M: int, R, channel: int):
+    _check(lib().firm_bin(plan, int(M), _ptr(R), int(channel)), "firm_bin")
+
+
+def firm_bin_info(plan):
+    """(n_work, n_points, bricks_per_axis, chunk) of the last firm_bin."""
+    v = [ctypes.c_int(0) for _ in range(4)]
+    _check(lib().firm_bin_info(plan, *[ctypes.byref(x) for x in v]), "firm_bin_info")
+    return tuple(int(x.value) for x in v)

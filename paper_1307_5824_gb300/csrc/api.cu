@@ -527,6 +527,7 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     else { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
     FIRM_CK(e);
     FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
+    P.bin_M = -1;
     tm.start(0);
     FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
     P.launches += M > 0 ? 1 : 0;
@@ -578,6 +579,7 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
         P.cur_images = images;
     }
     FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
+    P.bin_M = -1;
     tm.start(4);
     FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
     P.launches += M > 0 ? 1 : 0;
@@ -741,8 +743,49 @@ int firm_copy_out(firm_plan_t plan, int which, void* dst) {
         case FIRM_OUT_RHS: return P.have_rhs ? put_out(dst, P.ws.rhs, N * N * N * sizeof(float), P.stream) : FIRM_ESTATE;
         case FIRM_OUT_SAMPLES:
             return P.have_rhs ? put_out(dst, P.ws.samples, (size_t)P.p.M * P.nH * sizeof(float2), P.stream) : FIRM_ESTATE;
+        case FIRM_OUT_BIN_IDS:
+            if (P.bin_M < 0) return FIRM_ESTATE;
+            return put_out(dst, P.ws.payload, (size_t)P.bin_M * P.nH * sizeof(uint32_t), P.stream);
+        case FIRM_OUT_BIN_WORK: {
+            if (P.bin_M < 0) return FIRM_ESTATE;
+            int nw = 0;
+            FIRM_CK(cudaMemcpyAsync(&nw, P.ws.counters, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+            FIRM_CK(cudaStreamSynchronize(P.stream));
+            return put_out(dst, P.ws.work, (size_t)nw * sizeof(int4), P.stream);
+        }
         default: return FIRM_EINVAL;
     }
+}
+
+int firm_bin(firm_plan_t plan, int M, const double* R, int channel) {
+    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && !R) || (channel != 0 && channel != 1)) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    Workspace& w = P.ws;
+    cudaError_t e = cudaSuccess;
+    const double* Rd = stage(R, w.R, (size_t)M * 9, P.stream, e);
+    FIRM_CK(e);
+    FIRM_CK(launch_geom(Rd, M, w.geom, P.stream));
+    P.launches += M > 0 ? 1 : 0;
+    FIRM_CK(launch_bin(P, M, channel == 0));
+    P.bin_M = M;
+    P.bin_kc = channel == 0;
+    P.have_kernel = P.have_rhs = false;      // the ids share memory with the other stages' buffers
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    return FIRM_OK;
+}
+
+int firm_bin_info(firm_plan_t plan, int* n_work, int* n_points, int* bricks_per_axis, int* chunk) {
+    if (!plan) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (P.bin_M < 0) return FIRM_ESTATE;
+    int nw = 0;
+    FIRM_CK(cudaMemcpyAsync(&nw, P.ws.counters, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    if (n_work) *n_work = nw;
+    if (n_points) *n_points = P.bin_M * P.nH;
+    if (bricks_per_axis) *bricks_per_axis = P.bin_kc ? P.nbk : P.nbr;
+    if (chunk) *chunk = P.chunk;
+    return FIRM_OK;
 }
 
 int firm_launch_count(firm_plan_t plan, long long* out) {

@@ -144,6 +144,8 @@ struct Plan {
     float pc_axis[3] = {0, 0, 1};   // principal viewing axis of the last firm_kernel
     float ker0 = 1.0f;              // Ker(0) of the last firm_kernel
     int last_M = 0;                 // images of the last firm_kernel
+    int bin_M = -1;                 // images of the last firm_bin (its ids and items still held); -1 none
+    bool bin_kc = true;             // channel of the last firm_bin (true: kernel, 4N grid)
     // device pointers of the current call's inputs (caller's or staged copies)
     const double* cur_R = nullptr;
     const double* cur_shifts = nullptr;
