@@ -40,8 +40,10 @@ cudaError_t fft_init_constants() {
     return cudaMemcpyToSymbol(c_tw, h, sizeof(h));
 }
 
-constexpr int kTX = 16;          // lines per tile of a column pass
 constexpr int kThreads = 256;
+// Lines per tile of a column pass: enough that step 1 of the four-step FFT gives
+// every thread one item (lines x L2 = kThreads).
+template <int L> __host__ __device__ constexpr int TX() { return kThreads / Split<L>::L2; }
 
 // ---------------------------------------------------------------------------
 // Generic pass kernels.  An Op provides n_outer, n_inner / n_rows, tw, load, store.
@@ -49,10 +51,10 @@ constexpr int kThreads = 256;
 template <int L, int SIGN, class Op>
 __global__ void __launch_bounds__(kThreads) k_cols(const Op op) {
     extern __shared__ float2 S[];
-    const int tiles = (op.n_inner + kTX - 1) / kTX;
+    const int tiles = (op.n_inner + TX<L>() - 1) / TX<L>();
     const int outer = blockIdx.x / tiles;
-    const int c0 = (blockIdx.x % tiles) * kTX;
-    const int nl = min(kTX, op.n_inner - c0);
+    const int c0 = (blockIdx.x % tiles) * TX<L>();
+    const int nl = min(TX<L>(), op.n_inner - c0);
     auto ld = [&](int line, int n) { return op.load(outer, n, c0 + line); };
     auto st = [&](int line, int k, float2 v) { op.store(outer, k, c0 + line, v); };
     block_fft<L, SIGN, true>(nl, ld, st, S, op.tw);
@@ -74,10 +76,10 @@ __global__ void __launch_bounds__(kThreads) k_rows(Op op) {
 
 template <int L, int SIGN, class Op>
 static cudaError_t run_cols(const Op& op, cudaStream_t s) {
-    const size_t smem = sizeof(float2) * smem_elems<L, true>(kTX);
+    const size_t smem = sizeof(float2) * smem_elems<L, true>(TX<L>());
     cudaError_t e = cudaFuncSetAttribute(k_cols<L, SIGN, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int tiles = (op.n_inner + kTX - 1) / kTX;
+    const int tiles = (op.n_inner + TX<L>() - 1) / TX<L>();
     k_cols<L, SIGN, Op><<<op.n_outer * tiles, kThreads, smem, s>>>(op);
     return cudaGetLastError();
 }
@@ -445,15 +447,15 @@ struct TRowsInvOp {
     __device__ __forceinline__ void finish() const {}
 };
 
-// The z pass: forward, times K-hat, inverse; tile of kTX adjacent (j2, j1) columns.
+// The z pass: forward, times K-hat, inverse; tile of TX<L>() adjacent (j2, j1) columns.
 template <int L>
 __global__ void __launch_bounds__(kThreads) k_toep_z(float2* __restrict__ t2, const float* __restrict__ khat,
                                                      const float2* __restrict__ tw, int n_inner, int N,
                                                      const CgState* cg) {
     extern __shared__ float2 S[];
     if (cg && cg->done) return;
-    const int c0 = blockIdx.x * kTX;
-    const int nl = min(kTX, n_inner - c0);
+    const int c0 = blockIdx.x * TX<L>();
+    const int nl = min(TX<L>(), n_inner - c0);
     auto ld = [&](int line, int n) {
         return n < N ? t2[(size_t)n * n_inner + c0 + line] : make_float2(0.0f, 0.0f);
     };
@@ -542,10 +544,10 @@ template <int L, int SIGN, class Op>
 __global__ void __launch_bounds__(kThreads) k_cols_cg(const Op op, const CgState* cg) {
     extern __shared__ float2 S[];
     if (cg && cg->done) return;
-    const int tiles = (op.n_inner + kTX - 1) / kTX;
+    const int tiles = (op.n_inner + TX<L>() - 1) / TX<L>();
     const int outer = blockIdx.x / tiles;
-    const int c0 = (blockIdx.x % tiles) * kTX;
-    const int nl = min(kTX, op.n_inner - c0);
+    const int c0 = (blockIdx.x % tiles) * TX<L>();
+    const int nl = min(TX<L>(), op.n_inner - c0);
     auto ld = [&](int line, int n) { return op.load(outer, n, c0 + line); };
     auto st = [&](int line, int k, float2 v) { op.store(outer, k, c0 + line, v); };
     block_fft<L, SIGN, true>(nl, ld, st, S, op.tw);
@@ -558,7 +560,7 @@ static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, const float2* c
     const int N = P.N;
     constexpr int ROWS = rows_per_block<L>();
     const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
-    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
+    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(TX<L>());
     cudaError_t e;
     // pass 1: rows of x (or p = r + beta p), forward, half spectrum
     TRowsFwdOp a{{}, x, cg ? const_cast<float*>(x) : nullptr, cg_r, cg, w.t1, w.tw_2n, N * N, N, cg_z};
@@ -569,12 +571,12 @@ static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, const float2* c
     TColsYFwdOp b{w.t1, w.t2, w.tw_2n, N, N + 1, N};
     if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, TColsYFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
         return e;
-    const int tiles_b = (N + 1 + kTX - 1) / kTX;
+    const int tiles_b = (N + 1 + TX<L>() - 1) / TX<L>();
     k_cols_cg<L, -1, TColsYFwdOp><<<N * tiles_b, kThreads, smem_cols, P.stream>>>(b, cg);
     // pass 3: z forward x K-hat x z inverse
     const int n_inner = 2 * N * (N + 1);
     if ((e = cudaFuncSetAttribute(k_toep_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols))) return e;
-    k_toep_z<L><<<(n_inner + kTX - 1) / kTX, kThreads, smem_cols, P.stream>>>(w.t2, w.khat, w.tw_2n, n_inner, N, cg);
+    k_toep_z<L><<<(n_inner + TX<L>() - 1) / TX<L>(), kThreads, smem_cols, P.stream>>>(w.t2, w.khat, w.tw_2n, n_inner, N, cg);
     // pass 4: y inverse, keep y < N
     TColsYInvOp d{w.t2, w.t1, w.tw_2n, N, N + 1, N};
     if ((e = cudaFuncSetAttribute(k_cols_cg<L, +1, TColsYInvOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
@@ -632,8 +634,8 @@ __global__ void __launch_bounds__(kThreads) k_pc_z(float2* __restrict__ u, const
                                                    const float2* __restrict__ tw, int n_inner, const CgState* cg) {
     extern __shared__ float2 S[];
     if (cg->done) return;
-    const int c0 = blockIdx.x * kTX;
-    const int nl = min(kTX, n_inner - c0);
+    const int c0 = blockIdx.x * TX<L>();
+    const int nl = min(TX<L>(), n_inner - c0);
     auto ld = [&](int line, int n) { return u[(size_t)n * n_inner + c0 + line]; };
     auto mul = [&](int line, int k) { return __ldg(&d[(size_t)k * n_inner + c0 + line]); };
     auto st = [&](int line, int n, float2 v) { u[(size_t)n * n_inner + c0 + line] = v; };
@@ -730,7 +732,7 @@ static cudaError_t precond_l(Plan& P, const float2* r, float* z, CgState* cg) {
     constexpr int N = L, H = L / 2 + 1;
     constexpr int ROWS = rows_per_block<L>();
     const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
-    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
+    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(TX<L>());
     float2* u = w.t1;                       // N x N x (N/2+1) complex
     cudaError_t e;
     PRowsFwdOp a{{}, r, u, w.tw_n, N * N, N};
@@ -738,13 +740,13 @@ static cudaError_t precond_l(Plan& P, const float2* r, float* z, CgState* cg) {
         return e;
     k_rows_cg<L, PRowsFwdOp><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(a, cg);
     PColsYOp b{u, w.tw_n, N, H, N};
-    const int tiles = (H + kTX - 1) / kTX;
+    const int tiles = (H + TX<L>() - 1) / TX<L>();
     if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, PColsYOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
         return e;
     k_cols_cg<L, -1, PColsYOp><<<N * tiles, kThreads, smem_cols, P.stream>>>(b, cg);
     const int n_inner = N * H;
     if ((e = cudaFuncSetAttribute(k_pc_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols))) return e;
-    k_pc_z<L><<<(n_inner + kTX - 1) / kTX, kThreads, smem_cols, P.stream>>>(u, w.pc_diag, w.tw_n, n_inner, cg);
+    k_pc_z<L><<<(n_inner + TX<L>() - 1) / TX<L>(), kThreads, smem_cols, P.stream>>>(u, w.pc_diag, w.tw_n, n_inner, cg);
     if ((e = cudaFuncSetAttribute(k_cols_cg<L, +1, PColsYOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
         return e;
     k_cols_cg<L, +1, PColsYOp><<<N * tiles, kThreads, smem_cols, P.stream>>>(b, cg);
@@ -811,7 +813,7 @@ static cudaError_t chan_spectrum_l(Plan& P) {
     constexpr int N = L, H = L / 2 + 1;
     constexpr int ROWS = rows_per_block<L>();
     const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
-    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
+    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(TX<L>());
     float2* u = w.t1;
     cudaError_t e;
     k_chan_column<<<P.num_sms * 4, 256, 0, P.stream>>>(w.ker, w.r, N);
@@ -822,11 +824,11 @@ static cudaError_t chan_spectrum_l(Plan& P) {
     PColsYOp b{u, w.tw_n, N, H, N};
     if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, PColsYOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
         return e;
-    k_cols_cg<L, -1, PColsYOp><<<N * ((H + kTX - 1) / kTX), kThreads, smem_cols, P.stream>>>(b, nullptr);
+    k_cols_cg<L, -1, PColsYOp><<<N * ((H + TX<L>() - 1) / TX<L>()), kThreads, smem_cols, P.stream>>>(b, nullptr);
     PColsZOp c{u, w.tw_n, 1, N * H};
     if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, PColsZOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
         return e;
-    k_cols_cg<L, -1, PColsZOp><<<(N * H + kTX - 1) / kTX, kThreads, smem_cols, P.stream>>>(c, nullptr);
+    k_cols_cg<L, -1, PColsZOp><<<(N * H + TX<L>() - 1) / TX<L>(), kThreads, smem_cols, P.stream>>>(c, nullptr);
     P.launches += 4;
     return cudaGetLastError();
 }
@@ -895,7 +897,7 @@ static cudaError_t toeplitz_static_l(float2* scratch, const float* khat, const f
     if (e != cudaSuccess) return e;
     constexpr int ROWS = rows_per_block<L>();
     const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
-    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(kTX);
+    const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(TX<L>());
     TRowsFwdOp a{{}, x, nullptr, nullptr, nullptr, t1, tw, N * N, N};
     if ((e = cudaFuncSetAttribute(k_rows_cg<L, TRowsFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
         return e;
@@ -903,11 +905,11 @@ static cudaError_t toeplitz_static_l(float2* scratch, const float* khat, const f
     TColsYFwdOp b{t1, t2, tw, N, N + 1, N};
     if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, TColsYFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
         return e;
-    const int tiles_b = (N + 1 + kTX - 1) / kTX;
+    const int tiles_b = (N + 1 + TX<L>() - 1) / TX<L>();
     k_cols_cg<L, -1, TColsYFwdOp><<<N * tiles_b, kThreads, smem_cols, s>>>(b, nullptr);
     const int n_inner = 2 * N * (N + 1);
     if ((e = cudaFuncSetAttribute(k_toep_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols))) return e;
-    k_toep_z<L><<<(n_inner + kTX - 1) / kTX, kThreads, smem_cols, s>>>(t2, khat, tw, n_inner, N, nullptr);
+    k_toep_z<L><<<(n_inner + TX<L>() - 1) / TX<L>(), kThreads, smem_cols, s>>>(t2, khat, tw, n_inner, N, nullptr);
     TColsYInvOp d{t2, t1, tw, N, N + 1, N};
     if ((e = cudaFuncSetAttribute(k_cols_cg<L, +1, TColsYInvOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
         return e;

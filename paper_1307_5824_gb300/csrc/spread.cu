@@ -278,11 +278,24 @@ __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ paylo
         const int len = wk.z;
         if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            const uint8_t c = cls[wk.y + i];
-            s_ids[i] = payload[wk.y + i];
-            s_cls[i] = c;
-            atomicAdd(&s_hist[c], 1);
+        // four points per thread per step, all loads issued before the shared stores
+        for (int i0 = threadIdx.x; i0 < len; i0 += 4 * blockDim.x) {
+            uint8_t c[4];
+            uint32_t id[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < len) { c[u] = cls[wk.y + i]; id[u] = payload[wk.y + i]; }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < len) {
+                    s_ids[i] = id[u];
+                    s_cls[i] = c[u];
+                    atomicAdd(&s_hist[c[u]], 1);
+                }
+            }
         }
         __syncthreads();
         if (threadIdx.x < 32) {
