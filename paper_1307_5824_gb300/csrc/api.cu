@@ -157,6 +157,7 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.gid = c.take<int32_t>(M);
     w.geom = c.take<ImgGeom>(M);
     w.htab = c.take<int32_t>(nH);
+    w.colinfo = c.take<int4>(N / 2 + 1);
     w.h2 = c.take<float>(n_ctf * nH);
     w.h1 = c.take<float>(n_ctf * nH);
     w.tw_n = c.take<float2>(N);
@@ -491,6 +492,20 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
         if (e == cudaSuccess) e = cudaMemcpyAsync(d, s, b, cudaMemcpyHostToDevice, P.stream);
     };
     cp(w.htab, P.htab_host.data(), sizeof(int32_t) * nH);
+    // columns of the half disc in the order of htab: k1 = 0 holds k2 = 0..N/2, k1 > 0 holds -km..km
+    std::vector<int4> colv(N / 2 + 1);
+    {
+        int t0 = 0;
+        for (int k1 = 0; k1 <= N / 2; ++k1) {
+            int km = 0;
+            while ((km + 1) * (km + 1) + k1 * k1 <= (N / 2) * (N / 2)) ++km;
+            const int lo = k1 == 0 ? 0 : -km;
+            colv[k1] = make_int4(t0, lo, km, 0);
+            t0 += km - lo + 1;
+        }
+        if (t0 != nH) e = cudaErrorInvalidValue;
+    }
+    cp(w.colinfo, colv.data(), sizeof(int4) * colv.size());
     cp(w.h1, h1.data(), sizeof(float) * h1.size());
     cp(w.h2, h2.data(), sizeof(float) * h2.size());
     cp(w.tw_n, t1.data(), sizeof(float2) * N);

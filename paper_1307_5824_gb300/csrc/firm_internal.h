@@ -65,6 +65,7 @@ struct Workspace {
     // tables
     ImgGeom* geom = nullptr;
     int32_t* htab = nullptr;        // half-disc (k1, k2) packed as k1 | k2 << 16
+    int4* colinfo = nullptr;        // per k1 = 0..N/2: (first t of the column, lowest k2, highest k2, 0)
     float* h2 = nullptr;            // [group][t] h^2 (t = 0 halved)
     float* h1 = nullptr;            // [group][t] h
     float2* tw_n = nullptr;         // exp(-2 pi i j / L) for L = N, 2N, 4N

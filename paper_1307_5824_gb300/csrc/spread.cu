@@ -189,6 +189,48 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a, int M) {
     }
 }
 
+// Scatter pass with 2D patches: each warp takes a 4 x 8 patch of (k1, k2) of one image
+// (4 columns of the half disc, 8 consecutive k2 in each), so its 32 points cover a small
+// 2D piece of the slice and fall in few bricks; lanes with equal bricks are grouped
+// with __match_any_sync, one cursor atomic per group (about half as many as runs along
+// one column give).  col[k1] = (first index t of column k1, its lowest k2, its highest k2).
+template <int W>
+__global__ void __launch_bounds__(256) k_bin_scatter2d(BinArgs a, int M, int hN, const int4* __restrict__ col,
+                                                       int tiles_x, int n_tiles) {
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (tile >= n_tiles) return;                       // uniform over the warp
+    const int k1 = (tile % tiles_x) * 4 + (lane >> 3);
+    const int k2 = -hN + (tile / tiles_x) * 8 + (lane & 7);
+    int t = -1;
+    if (k1 <= hN) {
+        const int4 c = __ldg(&col[k1]);
+        if (k2 >= c.y && k2 <= c.z) t = c.x + (k2 - c.y);
+    }
+    const bool valid = t >= 0;
+    const int32_t kk = (int32_t)((uint32_t)(k1 & 0xffff) | ((uint32_t)k2 << 16));
+    for (int m = blockIdx.y; m < M; m += gridDim.y) {
+        int key = -1, c = 0;
+        if (valid) {
+            const PointPos p = point_pos(a.geom[m], kk, a.scale, a.halfG, a.G);
+            const int bx = p.I[0] / kBrick, by = p.I[1] / kBrick, bz = p.I[2] / kBrick;
+            key = (bz * a.nb + by) * a.nb + bx;
+            c = region_base<W>(p, bx * kBrick, by * kBrick, bz * kBrick) & 31;
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(grp) - 1;
+        uint32_t base = 0;
+        if (valid && lane == leader) base = atomicAdd(&a.count[key], (uint32_t)__popc(grp));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) {
+            const uint32_t slot = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+            a.payload[slot] = ((uint32_t)m << kTBits) | (uint32_t)t;
+            a.cls[slot] = (uint8_t)c;
+            if (a.samples) a.samples_b[slot] = __ldg(&a.samples[(size_t)m * a.nH + t]);
+        }
+    }
+}
+
 // Single-block scan over bricks: cursor = exclusive prefix of count; work items
 // (brick, start, length) of at most `chunk` points (chunk <= kChunk).
 __global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__ count, uint32_t* __restrict__ cursor,
@@ -367,7 +409,9 @@ static void bin_w(Plan& P, const BinArgs& a0, int nbricks, bool kc) {
     k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work,
                                           P.chunk);
     a.count = w.cursor;
-    k_bin<W, true><<<grid, 256, 0, P.stream>>>(a, M);
+    const int hN = P.N / 2, tiles_x = (hN + 1 + 3) / 4, n_tiles = tiles_x * ((P.N + 1 + 7) / 8);
+    const dim3 grid2((n_tiles + 7) / 8, (unsigned)(M < 65535 ? M : 65535));
+    k_bin_scatter2d<W><<<grid2, 256, 0, P.stream>>>(a, M, hN, w.colinfo, tiles_x, n_tiles);
     cudaFuncSetAttribute(k_class_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
     k_class_sort<<<P.num_sms * 4, 256, kSortSmem, P.stream>>>(w.payload, w.cls, w.work, w.counters,
                                                                kc ? nullptr : w.perm);
