@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--N", type=int, default=None, help="override volume edge (profiling of smaller cases)")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER, help="CG iteration cap (profiling)")
     ap.add_argument("--W", type=int, default=6)
-    ap.add_argument("--precond", default="learned", choices=["none", "circulant", "binned", "learned"])
+    ap.add_argument("--precond", default="learned", choices=["none", "circulant", "binned", "learned", "physics"],
+                    help="physics: the density-per-volume table alone (the learned network's baseline)")
+    ap.add_argument("--residual", action="store_true",
+                    help="learned: train on the target minus the density baseline (default: the raw table)")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-CG comparison run")
     ap.add_argument("--train-kernels", type=int, default=2000, help="N=64 kernels the learned preconditioner trains on")
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of the learned preconditioner")
@@ -162,6 +165,12 @@ def oracle_sample(inp, cg_iters: int, budget_images: int = 4000, n_vox: int = 2)
     sample = (f"oracle Ker and A*b (direct sums) at {n_vox} voxels over {Ms} of {M} images, one FP64 "
               f"circulant CG apply; extrapolated to (2N)^3 + N^3 voxels, {M} images, {cg_iters} iterations")
     return est, sample, {"ker_s_per_voxel": t_ker, "rhs_s_per_voxel": t_rhs, "cg_s_per_iter": t_it}
+
+
+def _features(rec):
+    f = np.empty(1024, np.float32)
+    rec.pc_features(f)
+    return f
 
 
 def cores_used():
@@ -377,21 +386,28 @@ def main():
         from paper_1307_5824_gb300 import learned
         t0 = time.perf_counter()
         X, T = learned.generate(args.train_kernels, N=64, m_range=(500, args.train_m_max), device=dev,
-                                defocus_um=np.linspace(1.0, 3.5, args.train_defocus), max_groups=args.train_groups)
+                                defocus_um=np.linspace(1.0, 3.5, args.train_defocus), max_groups=args.train_groups,
+                                residual=args.residual)
         t_gen = time.perf_counter() - t0
         net, hist = learned.train(X[: int(0.9 * len(X))], T[: int(0.9 * len(X))], steps=args.train_steps,
                                   lr_final=args.train_lr_final, device=dev)
         train_info = {"kernels": int(len(X)), "steps": args.train_steps, "gen_s": round(t_gen, 1), "loss": hist,
                       "val_mse_bf16": learned.evaluate(net, X[int(0.9 * len(X)):], T[int(0.9 * len(X)):], bf16=True)}
-    else:
+    elif args.precond != "physics":
         rec.set_precond(pc_modes[args.precond])
     x = torch.empty((N, N, N), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    base_tab = np.empty(1024, np.float32)
+    per_step_pc = {"on": True}          # the comparison run switches the per-step tables off
+
     def step(R_, g_, s_, im_, x_):
         rec.kernel(R_, g_)
-        if net is not None:
-            learned.apply_learned(rec, net)
+        if per_step_pc["on"] and net is not None:
+            learned.apply_learned(rec, net, residual=args.residual)
+        elif per_step_pc["on"] and args.precond == "physics":
+            rec.pc_baseline(base_tab)
+            rec.set_precond_table(base_tab)
         rec.backproject(im_, s_, R_, g_)
         st, it = rec.cg_solve(x_, args.max_iter, rel_tol=REL_TOL, allow=(L.FIRM_ENOTCONV,))
         return st, it
@@ -399,6 +415,15 @@ def main():
     for _ in range(max(3, args.warmup)):
         st, iters = step(R, gid, sh, img, x)
     torch.cuda.synchronize(dev)
+    if net is not None:
+        # how far the network's table is from its own target for this workload's kernel
+        tab = learned.predict(net, learned.net_input(_features(rec))[None], bf16=True)[0]
+        tgt = np.empty(1024, np.float32)
+        if args.residual:
+            rec.pc_residual_target(tgt)
+        else:
+            rec.pc_target(tgt)
+        train_info["table_vs_target_mse"] = float(((tab - tgt) ** 2).mean())
 
     # timed region: device-resident inputs; stage events recorded (no extra syncs)
     rec.set_timing(True)
@@ -452,8 +477,7 @@ def main():
     # the same reconstruction with plain CG (the comparison the metric names)
     plain = None
     if not args.no_compare and args.precond != "none":
-        net_saved = net
-        net = None
+        per_step_pc["on"] = False
         rec.set_precond(L.FIRM_PRECOND_NONE)
         for _ in range(2):
             st, it_pl = step(R, gid, sh, img, x)
@@ -472,7 +496,7 @@ def main():
         rec.set_timing(False)
         plain = {"s_per_recon": p0.elapsed_time(p1) / args.steps / 1e3, "cg_iters": int(np.median(it_plain)),
                  "cg_ms": cg_plain / args.steps}
-        net = net_saved
+        per_step_pc["on"] = True
 
     if rank != 0:
         if world > 1:

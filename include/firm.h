@@ -170,6 +170,21 @@ int firm_set_precond(firm_plan_t plan, int mode);
 int firm_pc_features(firm_plan_t plan, float* out1024);
 int firm_pc_target(firm_plan_t plan, float* out1024);
 int firm_pc_axis(firm_plan_t plan, float* out3);
+/* Fraction of the N^3 frequency grid (FFT index order, q in [-N/2, N/2)) falling in each
+ * of the 1024 (shell, cone) bins of the last firm_kernel's principal axis: 1024 float32,
+ * summing to 1.  With the density features f this gives the density per unit volume
+ * f_b / v_b, which for a sampling operator is the bin's mean eigenvalue / Ker(0). */
+int firm_pc_bin_volumes(firm_plan_t plan, float* out);
+/* A per-bin log table from the sampling density alone: t_b = -log(f_b / v_b + r), f the
+ * features (firm_pc_features), v the bin volumes, r the relative Tikhonov weight
+ * lambda_eff / Ker(0).  A closed-form estimate of the target of firm_pc_target (the
+ * bin's mean eigenvalue / Ker(0) is about f_b / v_b for a sampling operator); the
+ * learned preconditioner predicts the difference from it.  1024 float32. */
+int firm_pc_baseline(firm_plan_t plan, float* out);
+/* firm_pc_target minus firm_pc_baseline (what the learned preconditioner is trained on),
+ * and FIRM_PRECOND_TABLE set from baseline + delta (its prediction added back). */
+int firm_pc_residual_target(firm_plan_t plan, float* out);
+int firm_set_precond_residual(firm_plan_t plan, const float* delta);
 int firm_set_precond_table(firm_plan_t plan, const float* table_log1024);
 
 /* The network of the learned preconditioner: 1024 -> 256 -> 256 -> 1024 with ReLU, input
@@ -242,12 +257,13 @@ int firm_copy_out(firm_plan_t plan, int which, void* dst);
  *                      FIRM_OUT_SAMPLES), grouped by work item;
  *   FIRM_OUT_BIN_WORK  n_work work items, 4 int32 each: (brick, first id position,
  *                      point count, 0); brick = (bz * nb + by) * nb + bx;
- * and firm_bin_info gives n_work, M * |H|, nb (bricks per axis) and the most points of
- * an item.  Within an item the points are ordered round-robin over the 32 bank
+ * and firm_bin_info gives n_work, M * |H|, nb (bricks per axis along x and y), the
+ * brick depth along z in cells (bricks are 8 x 8 x depth) and the most points of an
+ * item.  Within an item the points are ordered round-robin over the 32 bank
  * classes of their first tap.  firm_bin reuses the memory of the kernel and A*b
  * results: call firm_kernel / firm_backproject again before using those. */
 int firm_bin(firm_plan_t plan, int M, const double* R, int channel);
-int firm_bin_info(firm_plan_t plan, int* n_work, int* n_points, int* bricks_per_axis, int* chunk);
+int firm_bin_info(firm_plan_t plan, int* n_work, int* n_points, int* bricks_per_axis, int* brick_depth, int* chunk);
 
 /* Device time of the last call of each stage, in milliseconds between CUDA events
  * recorded on the plan's stream around the stage (recorded only while timing is on,

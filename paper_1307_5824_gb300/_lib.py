@@ -26,7 +26,8 @@ EXPORTED = [
     "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_cg_solve",
     "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_set_precond", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
     "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_target", "firm_pc_axis",
-    "firm_set_precond_table", "firm_mlp_forward", "firm_mlp_to_bf16", "firm_mlp_forward_bf16", "firm_mlp_grad",
+    "firm_set_precond_table", "firm_pc_bin_volumes", "firm_pc_baseline", "firm_pc_residual_target", "firm_set_precond_residual",
+    "firm_mlp_forward", "firm_mlp_to_bf16", "firm_mlp_forward_bf16", "firm_mlp_grad",
     "firm_mlp_adam", "firm_mlp_param_count", "firm_mlp_work_floats",
     "firm_bin", "firm_bin_info",
     "firm_batch_workspace_size", "firm_batch_create", "firm_batch_run", "firm_batch_wait", "firm_batch_set_config",
@@ -84,7 +85,8 @@ def lib() -> ctypes.CDLL:
     L.firm_set_timing.argtypes = [vp, i]
     L.firm_stage_times.argtypes = [vp, ctypes.POINTER(d), i]
     L.firm_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
-    for n in ("firm_pc_features", "firm_pc_target", "firm_pc_axis", "firm_set_precond_table"):
+    for n in ("firm_pc_features", "firm_pc_target", "firm_pc_axis", "firm_set_precond_table", "firm_pc_bin_volumes", "firm_pc_baseline",
+              "firm_pc_residual_target", "firm_set_precond_residual"):
         getattr(L, n).argtypes = [vp, vp]
     L.firm_mlp_forward.argtypes = [vp, i, vp, vp, vp, vp]
     L.firm_mlp_to_bf16.argtypes = [vp, vp, vp]
@@ -95,7 +97,7 @@ def lib() -> ctypes.CDLL:
     L.firm_mlp_work_floats.argtypes = [i]
     L.firm_mlp_work_floats.restype = ctypes.c_size_t
     L.firm_bin.argtypes = [vp, i, vp, i]
-    L.firm_bin_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.firm_bin_info.argtypes = [vp] + [ctypes.POINTER(i)] * 5
     L.firm_batch_workspace_size.argtypes = [i, ctypes.POINTER(ctypes.c_size_t)]
     L.firm_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), i, vp, ctypes.c_size_t, vp]
     L.firm_batch_run.argtypes = [vp, ctypes.POINTER(firm_batch_item), i, i]
@@ -361,7 +363,23 @@ def firm_bin(plan, M: int, R, channel: int):
 
 
 def firm_bin_info(plan):
-    """(n_work, n_points, bricks_per_axis, chunk) of the last firm_bin."""
-    v = [ctypes.c_int(0) for _ in range(4)]
+    """(n_work, n_points, bricks_per_axis, brick_depth, chunk) of the last firm_bin."""
+    v = [ctypes.c_int(0) for _ in range(5)]
     _check(lib().firm_bin_info(plan, *[ctypes.byref(x) for x in v]), "firm_bin_info")
     return tuple(int(x.value) for x in v)
+
+
+def firm_pc_bin_volumes(plan, out):
+    _check(lib().firm_pc_bin_volumes(plan, _ptr(out)), "firm_pc_bin_volumes")
+
+
+def firm_pc_baseline(plan, out):
+    _check(lib().firm_pc_baseline(plan, _ptr(out)), "firm_pc_baseline")
+
+
+def firm_pc_residual_target(plan, out):
+    _check(lib().firm_pc_residual_target(plan, _ptr(out)), "firm_pc_residual_target")
+
+
+def firm_set_precond_residual(plan, delta):
+    _check(lib().firm_set_precond_residual(plan, _ptr(delta)), "firm_set_precond_residual")

@@ -435,6 +435,7 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
     P.Gk = 4 * p->N;
     P.Gr = 2 * p->N;
     P.nbk = P.Gk / kBrick;
+    P.nbkz = P.Gk / kBrickZk;
     P.nbr = P.Gr / kBrick;
     P.nK = disc_size(p->N);
     P.nH = (P.nK + 1) / 2;
@@ -734,6 +735,90 @@ int firm_pc_target(firm_plan_t plan, float* out) {
     return put_out(out, P.ws.pc_s1, 1024 * sizeof(float), P.stream);
 }
 
+// Density-per-volume baseline of the log table: the mean eigenvalue of a sampling
+// operator over a bin is about Ker(0) f_b / v_b, so log(p_b Ker(0)) ~ -log(f_b / v_b +
+// lambda / Ker(0)) with lambda / Ker(0) = 1e-3 (the relative Tikhonov weight).
+int firm_pc_baseline(firm_plan_t plan, float* out) {
+    if (!plan || !out) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!P.have_kernel) return FIRM_ESTATE;
+    std::vector<float> f(1024), v(1024), t(1024);
+    int st = firm_pc_features(plan, f.data());
+    if (st != FIRM_OK) return st;
+    st = firm_pc_bin_volumes(plan, v.data());
+    if (st != FIRM_OK) return st;
+    const double rl = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda : P.p.lambda / (double)P.ker0;
+    for (int b = 0; b < 1024; ++b)
+        t[b] = (float)-std::log((v[b] > 0.0f ? (double)f[b] / (double)v[b] : 0.0) + (rl > 0.0 ? rl : 1e-6));
+    if (is_device(out)) {
+        FIRM_CK(cudaMemcpyAsync(out, t.data(), 1024 * sizeof(float), cudaMemcpyHostToDevice, P.stream));
+        FIRM_CK(cudaStreamSynchronize(P.stream));
+    } else {
+        std::memcpy(out, t.data(), 1024 * sizeof(float));
+    }
+    return FIRM_OK;
+}
+
+static int to_host(const float* src, float* dst, size_t n, cudaStream_t s) {
+    if (is_device(src)) {
+        FIRM_CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        FIRM_CK(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(dst, src, n * sizeof(float));
+    }
+    return FIRM_OK;
+}
+
+static int from_host(const float* src, float* dst, size_t n, cudaStream_t s) {
+    if (is_device(dst)) {
+        FIRM_CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyHostToDevice, s));
+        FIRM_CK(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(dst, src, n * sizeof(float));
+    }
+    return FIRM_OK;
+}
+
+int firm_pc_residual_target(firm_plan_t plan, float* out) {
+    if (!plan || !out) return FIRM_EINVAL;
+    std::vector<float> t(1024), b(1024);
+    int st = firm_pc_target(plan, t.data());
+    if (st == FIRM_OK) st = firm_pc_baseline(plan, b.data());
+    if (st != FIRM_OK) return st;
+    for (int k = 0; k < 1024; ++k) t[k] -= b[k];
+    return from_host(t.data(), out, 1024, plan->P.stream);
+}
+
+int firm_set_precond_residual(firm_plan_t plan, const float* delta) {
+    if (!plan || !delta) return FIRM_EINVAL;
+    std::vector<float> d(1024), b(1024);
+    int st = to_host(delta, d.data(), 1024, plan->P.stream);
+    if (st == FIRM_OK) st = firm_pc_baseline(plan, b.data());
+    if (st != FIRM_OK) return st;
+    for (int k = 0; k < 1024; ++k) b[k] += d[k];
+    return firm_set_precond_table(plan, b.data());
+}
+
+int firm_pc_bin_volumes(firm_plan_t plan, float* out) {
+    if (!plan || !out) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!P.have_kernel) return FIRM_ESTATE;
+    FIRM_CK(launch_pc_bin_counts(P, P.ws.pc_s1, P.ws.pc_s2));
+    std::vector<double> c(1024);
+    FIRM_CK(cudaMemcpyAsync(c.data(), P.ws.pc_s1, 1024 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    FIRM_CK(cudaStreamSynchronize(P.stream));
+    const double n3 = (double)P.N * P.N * P.N;
+    std::vector<float> v(1024);
+    for (int b = 0; b < 1024; ++b) v[b] = (float)(c[b] / n3);
+    if (is_device(out)) {
+        FIRM_CK(cudaMemcpyAsync(out, v.data(), 1024 * sizeof(float), cudaMemcpyHostToDevice, P.stream));
+        FIRM_CK(cudaStreamSynchronize(P.stream));
+    } else {
+        std::memcpy(out, v.data(), 1024 * sizeof(float));
+    }
+    return FIRM_OK;
+}
+
 int firm_pc_axis(firm_plan_t plan, float* out3) {
     if (!plan || !out3) return FIRM_EINVAL;
     if (!plan->P.have_kernel) return FIRM_ESTATE;
@@ -789,7 +874,7 @@ int firm_bin(firm_plan_t plan, int M, const double* R, int channel) {
     return FIRM_OK;
 }
 
-int firm_bin_info(firm_plan_t plan, int* n_work, int* n_points, int* bricks_per_axis, int* chunk) {
+int firm_bin_info(firm_plan_t plan, int* n_work, int* n_points, int* bricks_per_axis, int* brick_depth, int* chunk) {
     if (!plan) return FIRM_EINVAL;
     Plan& P = plan->P;
     if (P.bin_M < 0) return FIRM_ESTATE;
@@ -799,6 +884,7 @@ int firm_bin_info(firm_plan_t plan, int* n_work, int* n_points, int* bricks_per_
     if (n_work) *n_work = nw;
     if (n_points) *n_points = P.bin_M * P.nH;
     if (bricks_per_axis) *bricks_per_axis = P.bin_kc ? P.nbk : P.nbr;
+    if (brick_depth) *brick_depth = P.bin_kc ? kBrickZk : kBrick;
     if (chunk) *chunk = P.chunk;
     return FIRM_OK;
 }

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_pc_target_sums(const float2* __restrict
         const int k1 = (int)(i % H), k2 = (int)((i / H) % N), k3 = (int)(i / ((long long)H * N));
         const float q1 = (float)k1, q2 = (float)(k2 < N / 2 ? k2 : k2 - N), q3 = (float)(k3 < N / 2 ? k3 : k3 - N);
         const float w = (k1 == 0 || k1 == N / 2) ? 1.0f : 2.0f;
-        const float kap = fmaxf(u[i].x, 0.0f) + lam;
+        const float kap = u ? fmaxf(u[i].x, 0.0f) + lam : 1.0f;     // u == nullptr: count frequencies
         const int b = freq_bin(q1, q2, q3, 0.5f * N, a1, a2, a3);
         atomicAdd(&sh1[b], w * kap);
         atomicAdd(&sh2[b], w * kap * kap);
@@ -185,6 +185,17 @@ cudaError_t launch_pc_target_sums(Plan& P, double* s1, double* s2) {
     if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, sizeof(double) * kBins, P.stream);
     if (e != cudaSuccess) return e;
     k_pc_target_sums<<<P.num_sms * 2, 256, 0, P.stream>>>(P.ws.t1, P.N, (float)P.lam_eff, P.pc_axis[0], P.pc_axis[1],
+                                                          P.pc_axis[2], s1, s2);
+    P.launches += 1;
+    return cudaGetLastError();
+}
+
+// Frequencies of the N^3 grid per bin (s1 = s2 = count), for bin volumes.
+cudaError_t launch_pc_bin_counts(Plan& P, double* s1, double* s2) {
+    cudaError_t e = cudaMemsetAsync(s1, 0, kBins * sizeof(double), P.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, kBins * sizeof(double), P.stream);
+    if (e != cudaSuccess) return e;
+    k_pc_target_sums<<<P.num_sms * 2, 256, 0, P.stream>>>(nullptr, P.N, 0.0f, P.pc_axis[0], P.pc_axis[1],
                                                           P.pc_axis[2], s1, s2);
     P.launches += 1;
     return cudaGetLastError();

@@ -116,15 +116,19 @@ __device__ __forceinline__ void window_taps(const KbPoly& P, float f, float* w) 
     }
 }
 
-// Index of the first tap of a point inside its brick's (16 + W)^3 region, or -1 if
-// the point is not inside the brick (never expected: binning uses the same code).
-template <int W>
+// Bricks: 8 x 8 x BZ cells (BZ = kBrickZk for the kernel channel, 8 for A*b).
+template <bool KC> struct Brick { static constexpr int BZ = KC ? kBrickZk : kBrick; };
+
+// Index of the first tap of a point inside its brick's (8 + W) x (8 + W) x (BZ + W)
+// region (x fastest), or -1 if the point is not inside the brick (never expected:
+// binning uses the same code).
+template <int W, int BZ>
 __device__ __forceinline__ int region_base(const PointPos& p, int lo0, int lo1, int lo2) {
     constexpr int RG = kBrick + W;
     const int r0 = p.I[0] - lo0 + tap_shift<W>(p.f[0]);
     const int r1 = p.I[1] - lo1 + tap_shift<W>(p.f[1]);
     const int r2 = p.I[2] - lo2 + tap_shift<W>(p.f[2]);
-    if ((unsigned)r0 > (unsigned)kBrick || (unsigned)r1 > (unsigned)kBrick || (unsigned)r2 > (unsigned)kBrick)
+    if ((unsigned)r0 > (unsigned)kBrick || (unsigned)r1 > (unsigned)kBrick || (unsigned)r2 > (unsigned)BZ)
         return -1;
     return (r2 * RG + r1) * RG + r0;
 }
@@ -150,8 +154,9 @@ struct BinArgs {
     float scale;
 };
 
-template <int W, bool SCATTER>
+template <int W, bool SCATTER, bool KC>
 __global__ void __launch_bounds__(256) k_bin(BinArgs a, int M) {
+    constexpr int BZ = Brick<KC>::BZ;
     // x: samples t of one image (consecutive lanes walk a column of the half disc);
     // y: images.  Runs of equal bricks among consecutive lanes are aggregated.
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,9 +166,9 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a, int M) {
         int key = -1, c = 0;
         if (valid) {
             const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
-            const int bx = p.I[0] / kBrick, by = p.I[1] / kBrick, bz = p.I[2] / kBrick;
+            const int bx = p.I[0] / kBrick, by = p.I[1] / kBrick, bz = p.I[2] / BZ;
             key = (bz * a.nb + by) * a.nb + bx;
-            if (SCATTER) c = region_base<W>(p, bx * kBrick, by * kBrick, bz * kBrick) & 31;
+            if (SCATTER) c = region_base<W, BZ>(p, bx * kBrick, by * kBrick, bz * BZ) & 31;
         }
         const int prev = __shfl_up_sync(0xffffffffu, key, 1);
         const bool head = (lane == 0) || (prev != key);
@@ -194,9 +199,10 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a, int M) {
 // 2D piece of the slice and fall in few bricks; lanes with equal bricks are grouped
 // with __match_any_sync, one cursor atomic per group (about half as many as runs along
 // one column give).  col[k1] = (first index t of column k1, its lowest k2, its highest k2).
-template <int W>
+template <int W, bool KC>
 __global__ void __launch_bounds__(256) k_bin_scatter2d(BinArgs a, int M, int hN, const int4* __restrict__ col,
                                                        int tiles_x, int n_tiles) {
+    constexpr int BZ = Brick<KC>::BZ;
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (tile >= n_tiles) return;                       // uniform over the warp
@@ -213,9 +219,9 @@ __global__ void __launch_bounds__(256) k_bin_scatter2d(BinArgs a, int M, int hN,
         int key = -1, c = 0;
         if (valid) {
             const PointPos p = point_pos(a.geom[m], kk, a.scale, a.halfG, a.G);
-            const int bx = p.I[0] / kBrick, by = p.I[1] / kBrick, bz = p.I[2] / kBrick;
+            const int bx = p.I[0] / kBrick, by = p.I[1] / kBrick, bz = p.I[2] / BZ;
             key = (bz * a.nb + by) * a.nb + bx;
-            c = region_base<W>(p, bx * kBrick, by * kBrick, bz * kBrick) & 31;
+            c = region_base<W, BZ>(p, bx * kBrick, by * kBrick, bz * BZ) & 31;
         }
         const unsigned grp = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(grp) - 1;
@@ -405,13 +411,15 @@ static void bin_w(Plan& P, const BinArgs& a0, int nbricks, bool kc) {
     BinArgs a = a0;
     const int M = (int)(a.npts / a.nH);
     const dim3 grid((a.nH + 255) / 256, (unsigned)(M < 65535 ? M : 65535));
-    k_bin<W, false><<<grid, 256, 0, P.stream>>>(a, M);
+    if (kc) k_bin<W, false, true><<<grid, 256, 0, P.stream>>>(a, M);
+    else k_bin<W, false, false><<<grid, 256, 0, P.stream>>>(a, M);
     k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work,
                                           P.chunk);
     a.count = w.cursor;
     const int hN = P.N / 2, tiles_x = (hN + 1 + 3) / 4, n_tiles = tiles_x * ((P.N + 1 + 7) / 8);
     const dim3 grid2((n_tiles + 7) / 8, (unsigned)(M < 65535 ? M : 65535));
-    k_bin_scatter2d<W><<<grid2, 256, 0, P.stream>>>(a, M, hN, w.colinfo, tiles_x, n_tiles);
+    if (kc) k_bin_scatter2d<W, true><<<grid2, 256, 0, P.stream>>>(a, M, hN, w.colinfo, tiles_x, n_tiles);
+    else k_bin_scatter2d<W, false><<<grid2, 256, 0, P.stream>>>(a, M, hN, w.colinfo, tiles_x, n_tiles);
     cudaFuncSetAttribute(k_class_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
     k_class_sort<<<P.num_sms * 4, 256, kSortSmem, P.stream>>>(w.payload, w.cls, w.work, w.counters,
                                                                kc ? nullptr : w.perm);
@@ -421,7 +429,7 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
     Workspace& w = P.ws;
     const int G = kc ? P.Gk : P.Gr;
     const int nb = kc ? P.nbk : P.nbr;
-    const int nbricks = nb * nb * nb;
+    const int nbricks = nb * nb * (kc ? P.nbkz : P.nbr);
     cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * nbricks, P.stream);
     if (e != cudaSuccess) return e;
     BinArgs a;
@@ -499,7 +507,8 @@ __device__ __forceinline__ float2 point_weight(const SpreadArgs& a, bool cplx, i
 // taps between folds, so a tap is scaled to at most 2^30 / (256 * PPR): 2^21 for the
 // A*b channel (PPR 2) and 2^20 for the kernel channel (PPR 4, half the barriers; the
 // extra bit of rounding takes Ker's fixed-point error from ~6e-7 to ~1.2e-6, still
-// well below the window's own ~5e-6 at W=6).
+// well below the window's own ~5e-6 at W=6; for A*b it would double the fixed-point
+// error to ~3e-6 for a 1% gain, so A*b keeps PPR 2).
 template <bool CPLX> struct SpreadRound { static constexpr int PPR = CPLX ? 2 : 4; static constexpr int kScaleBits = CPLX ? 21 : 20; };
 
 // One work item (a piece of one brick's points) into the brick's shared-memory region,
@@ -507,15 +516,16 @@ template <bool CPLX> struct SpreadRound { static constexpr int PPR = CPLX ? 2 : 
 template <int W, bool CPLX>
 __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& poly, const int4 wk, int* lev1,
                                              float* lev2, float* s_red) {
+    constexpr int BZ = Brick<!CPLX>::BZ;           // the kernel channel is the real one
     constexpr int RG = kBrick + W;
-    constexpr int RG3 = RG * RG * RG;
+    constexpr int RG3 = RG * RG * (BZ + W);
     constexpr int NC = CPLX ? 2 : 1;
     constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
     constexpr int kMagicBits = 0x4B400000;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b = wk.x;
     const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
-    const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * kBrick;
+    const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * BZ;
     // the piece is ordered round-robin over bank classes: thread i takes points
     // i, i + 256, ... (every thread the same count, up to one)
     const uint32_t s0 = (uint32_t)wk.y + threadIdx.x;
@@ -550,7 +560,7 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
             const int m = (int)(id >> kTBits);
             const int t = (int)(id & ((1u << kTBits) - 1u));
             const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
-            const int base = region_base<W>(p, lo0, lo1, lo2);
+            const int base = region_base<W, BZ>(p, lo0, lo1, lo2);
             if (base < 0) {
                 atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
                 continue;
@@ -615,14 +625,14 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
 
 template <int W, bool CPLX>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
-    constexpr int RG = kBrick + W;
     constexpr int NC = CPLX ? 2 : 1;
+    constexpr int R3 = (kBrick + W) * (kBrick + W) * (Brick<!CPLX>::BZ + W);
     extern __shared__ int sm_i[];
-    int* lev1 = sm_i;                                  // NC * RG^3 int32
-    float* lev2 = reinterpret_cast<float*>(sm_i + NC * RG * RG * RG);   // NC * RG^3 float
+    int* lev1 = sm_i;                                  // NC * R3 int32
+    float* lev2 = reinterpret_cast<float*>(sm_i + NC * R3);   // NC * R3 float
     __shared__ int s_item;
     __shared__ float s_red[kSpreadWarps];
-    for (int i = threadIdx.x; i < 2 * NC * RG * RG * RG; i += blockDim.x) sm_i[i] = 0;
+    for (int i = threadIdx.x; i < 2 * NC * R3; i += blockDim.x) sm_i[i] = 0;
     const int n_work = a.counters[0];
     for (;;) {
         __syncthreads();
@@ -640,14 +650,14 @@ template <int W, bool CPLX>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread_batch(const SpreadArgs* __restrict__ desc, int n,
                                                                  const int* __restrict__ item_off, int* queue,
                                                                  const KbPoly poly) {
-    constexpr int RG = kBrick + W;
     constexpr int NC = CPLX ? 2 : 1;
+    constexpr int R3 = (kBrick + W) * (kBrick + W) * (Brick<!CPLX>::BZ + W);
     extern __shared__ int sm_i[];
     int* lev1 = sm_i;
-    float* lev2 = reinterpret_cast<float*>(sm_i + NC * RG * RG * RG);
+    float* lev2 = reinterpret_cast<float*>(sm_i + NC * R3);
     __shared__ int s_item, s_prob;
     __shared__ float s_red[kSpreadWarps];
-    for (int i = threadIdx.x; i < 2 * NC * RG * RG * RG; i += blockDim.x) sm_i[i] = 0;
+    for (int i = threadIdx.x; i < 2 * NC * R3; i += blockDim.x) sm_i[i] = 0;
     const int total = item_off[n];
     for (;;) {
         __syncthreads();
@@ -694,8 +704,8 @@ __global__ void k_batch_items(const SpreadArgs* __restrict__ desc, int n, int* _
 
 template <int W, bool CPLX>
 static size_t spread_smem() {
-    constexpr int RG = kBrick + W;
-    return sizeof(int) * RG * RG * RG * (CPLX ? 2 : 1) * 2;
+    constexpr int R3 = (kBrick + W) * (kBrick + W) * (Brick<!CPLX>::BZ + W);
+    return sizeof(int) * R3 * (CPLX ? 2 : 1) * 2;
 }
 
 template <int W, bool CPLX>

@@ -46,9 +46,12 @@ def net_input(feat: np.ndarray) -> np.ndarray:
 
 
 def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3000), device="cuda:0",
-             defocus_um=DEFOCUS_UM, max_groups: int = 4):
+             defocus_um=DEFOCUS_UM, max_groups: int = 4, residual: bool = False):
     """(X, T): network inputs and targets of n_kernels method-generated kernels; each
-    kernel uses 1..max_groups of the defocus values."""
+    kernel uses 1..max_groups of the defocus values.  With residual, T is the target
+    minus the density-per-volume baseline (firm_pc_baseline), for a network that learns
+    only the correction (an option: the baseline is extreme in bins with few grid
+    frequencies, and the raw table trains better)."""
     rng = np.random.default_rng(seed)
     defocus_um = np.asarray(defocus_um, float)
     groups = synth.ctf_group_table(defocus_um)
@@ -64,7 +67,10 @@ def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3
         gid = sub[rng.integers(0, len(sub), M)].astype(np.int32)
         rec.kernel(np.ascontiguousarray(R.reshape(M, 9)), gid, M=M)
         rec.pc_features(f)
-        rec.pc_target(t)
+        if residual:
+            rec.pc_residual_target(t)
+        else:
+            rec.pc_target(t)
         X[i] = net_input(f)
         T[i] = t
     rec.close()
@@ -137,10 +143,14 @@ def predict(params: torch.Tensor, X: np.ndarray, bf16: bool = True) -> np.ndarra
     return y.cpu().numpy()
 
 
-def apply_learned(rec: Reconstructor, params: torch.Tensor, bf16: bool = True) -> np.ndarray:
-    """Features of the plan's last kernel -> network -> FIRM_PRECOND_TABLE.  Returns the table."""
+def apply_learned(rec: Reconstructor, params: torch.Tensor, bf16: bool = True, residual: bool = False) -> np.ndarray:
+    """Features of the plan's last kernel -> network (+ the density baseline when the
+    network was trained on residuals) -> FIRM_PRECOND_TABLE.  Returns the table."""
     f = np.empty(NBINS, np.float32)
     rec.pc_features(f)
-    table = predict(params, net_input(f)[None], bf16=bf16)[0]
-    rec.set_precond_table(np.ascontiguousarray(table))
-    return table
+    out = predict(params, net_input(f)[None], bf16=bf16)[0]
+    if residual:
+        rec.set_precond_residual(np.ascontiguousarray(out))
+    else:
+        rec.set_precond_table(np.ascontiguousarray(out))
+    return out

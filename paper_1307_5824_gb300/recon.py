@@ -54,6 +54,18 @@ class Reconstructor:
     def pc_target(self, out):
         L.firm_pc_target(self.plan, out)
 
+    def pc_residual_target(self, out):
+        L.firm_pc_residual_target(self.plan, out)
+
+    def set_precond_residual(self, delta):
+        L.firm_set_precond_residual(self.plan, delta)
+
+    def pc_baseline(self, out):
+        L.firm_pc_baseline(self.plan, out)
+
+    def pc_bin_volumes(self, out):
+        L.firm_pc_bin_volumes(self.plan, out)
+
     def pc_axis(self):
         return L.firm_pc_axis(self.plan)
 

@@ -1,5 +1,6 @@
 """The binning step (slice geometry of eq. forward-projector; points grouped per brick of
-the fine grid before spreading, Section 3.4) checked exactly: the ids are a permutation
+the fine grid before spreading, Section 3.4; bricks of 8 x 8 x depth cells, the depth
+reported by firm_bin_info) checked exactly: the ids are a permutation
 of all points, the work items tile the id array, every point sits in its item's brick
 (positions recomputed in FP64 from the rotations; points within 1e-4 cells of a brick
 face may go either way), no item exceeds the work-item size, and within every item the
@@ -46,7 +47,8 @@ def test_binning_is_an_exact_partition_by_brick(F, channel):
     inp = synth.config_inputs("C2", M=M, N=N, images=False)
     rec = F.Reconstructor(N, M, W=W)
     F._lib.firm_bin(rec.plan, M, torch.from_numpy(inp["R"].reshape(M, 9).copy()).cuda(), channel)
-    n_work, n_pts, nb, chunk = F._lib.firm_bin_info(rec.plan)
+    n_work, n_pts, nb, bzd, chunk = F._lib.firm_bin_info(rec.plan)
+    assert bzd in (8, 16)
     ids = torch.empty(n_pts, dtype=torch.int32, device="cuda")
     work = torch.empty((n_work, 4), dtype=torch.int32, device="cuda")
     F._lib.firm_copy_out(rec.plan, F._lib.FIRM_OUT_BIN_IDS, ids)
@@ -80,7 +82,7 @@ def test_binning_is_an_exact_partition_by_brick(F, channel):
     cell = fl.astype(np.int64) % G
     frac = y - fl
     near = np.any(np.minimum(frac, 1 - frac) < 1e-4, axis=1)                   # too close to a cell face
-    bxyz = cell // 8
+    bxyz = cell // np.array([8, 8, bzd])
     brick_of_pos = np.empty(n_pts, np.int64)
     for w_ in work:
         brick_of_pos[w_[1]:w_[1] + w_[2]] = w_[0]
@@ -88,9 +90,10 @@ def test_binning_is_an_exact_partition_by_brick(F, channel):
     ok = (bxyz[:, 0] == bx) & (bxyz[:, 1] == by) & (bxyz[:, 2] == bz)
     assert np.all(ok | near), int((~(ok | near)).sum())
 
-    # bank classes: first tap r = cell - 8 * brick + ceil(frac) (even W), base in a (8+W)^3 region
+    # bank classes: first tap r = cell - brick origin + ceil(frac) (even W), base in an
+    # (8+W) x (8+W) x (depth+W) region, x fastest
     RG = 8 + W
-    r = cell - 8 * np.stack([bx, by, bz], 1) + np.ceil(frac).astype(np.int64)
+    r = cell - np.array([8, 8, bzd]) * np.stack([bx, by, bz], 1) + np.ceil(frac).astype(np.int64)
     cls = ((r[:, 2] * RG + r[:, 1]) * RG + r[:, 0]) % 32
     checked = 0
     for w_ in work:

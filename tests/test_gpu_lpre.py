@@ -56,6 +56,25 @@ def test_features_axis_and_target_match_oracle(F):
     rec.close()
 
 
+def test_bin_volumes_and_baseline_match_oracle(F):
+    N, M = 16, 60
+    inp, rec = _plan(F, N, M)
+    a_g = rec.pc_axis().astype(np.float64)
+    a_g /= np.linalg.norm(a_g)
+    v = np.empty(1024, np.float32)
+    rec.pc_bin_volumes(v)
+    v_o = LP.bin_volumes(N, a_g)
+    assert abs(v.sum() - 1.0) <= 1e-6
+    assert np.abs(v - v_o).sum() <= 2e-3            # frequencies on a cone edge may move
+    f = np.empty(1024, np.float32)
+    rec.pc_features(f)
+    b = np.empty(1024, np.float32)
+    rec.pc_baseline(b)
+    b_o = LP.baseline(f.astype(np.float64), v.astype(np.float64), 1e-3)
+    assert np.abs(b - b_o).max() <= 1e-4
+    rec.close()
+
+
 def test_mlp_gradient_and_bf16_forward_match_oracle(F):
     L = F._lib
     rng = np.random.default_rng(60)

@@ -604,3 +604,24 @@ def test_c1_fp32_fft_drift():
     xo, _, _ = O.cg(lambda v: O.toeplitz_apply(Kh, v).real, rhs, 10)
     drift = np.linalg.norm(x - xo) / np.linalg.norm(xo)
     assert 2e-5 <= drift <= 3e-4, drift
+
+
+def test_bin_volumes_partition_the_grid_and_baseline_of_uniform_density():
+    """Learned-preconditioner baseline: the bin volumes are the fractions of the N^3 grid
+    per bin (they sum to 1 and equal a direct count), and a density proportional to the
+    volumes (f = v) gives the constant table -log(1 + lambda / Ker(0))."""
+    from oracle import lpre as LP
+    N = 8
+    a = np.array([0.3, -0.2, 0.93])
+    a /= np.linalg.norm(a)
+    v = LP.bin_volumes(N, a)
+    assert abs(v.sum() - 1.0) < 1e-12
+    cnt = np.zeros(LP.NBINS)
+    for i in range(N):
+        for j in range(N):
+            for k in range(N):
+                q = np.array([[(k + N // 2) % N - N // 2, (j + N // 2) % N - N // 2, (i + N // 2) % N - N // 2]], float)
+                cnt[LP.bin_index(q, N, a)[0]] += 1
+    assert np.allclose(v * N ** 3, cnt)
+    b = LP.baseline(v, v, 1e-3)
+    assert np.allclose(b[v > 0], -np.log(1.001))
