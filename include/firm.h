@@ -125,6 +125,20 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
 int firm_backproject(firm_plan_t plan, int M, const void* images, const double* shifts,
                      const double* R, const int32_t* group, float* rhs_out);
 
+/* Upload of host images ahead of firm_backproject (Section 3.4, step 1's input), so
+ * that the copy overlaps firm_kernel, which does not read the images.  Starts copying
+ * M host images (images: host memory, M x N x N in the plan's image type, row major;
+ * page-locked for the copy to run asynchronously) into `staging` (device memory owned
+ * by the caller, at least M * N * N * element-size bytes) on a copy stream of the
+ * plan, and returns without waiting.  The next firm_backproject of this plan called
+ * with the same host pointer and the same M orders itself after the copy and reads
+ * the staged images; any other call copies as usual.  The caller keeps `images` and
+ * `staging` unchanged until that firm_backproject has returned.  A later stage waits
+ * for the previous staged images to be read.  firm_destroy waits for a pending copy.
+ * FIRM_EINVAL: M < 0 or above the plan's M, a null pointer with M > 0, images in
+ * device memory, staging not in device memory or too small. */
+int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging, size_t staging_bytes);
+
 /* FIRM step 4 (Section 3.3): conjugate gradients on (A*A + lam_eff I) x = rhs from
  * x = 0, with FP64 step lengths and residual recurrence.  rhs may be NULL (use the
  * A*b kept by firm_backproject).  Runs max_iter iterations, or stops once the

@@ -23,7 +23,7 @@ FIRM_BATCH_GRAPH, FIRM_BATCH_PERSISTENT = 1, 2
 FIRM_FLAG_FP64_CG = 1
 
 EXPORTED = [
-    "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_cg_solve",
+    "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_stage_images", "firm_cg_solve",
     "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_set_precond", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
     "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_target", "firm_pc_axis",
     "firm_set_precond_table", "firm_pc_bin_volumes", "firm_pc_baseline", "firm_pc_residual_target", "firm_set_precond_residual",
@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
                             vp, ctypes.c_size_t, vp]
     L.firm_kernel.argtypes = [vp, i, vp, vp, vp]
     L.firm_backproject.argtypes = [vp, i, vp, vp, vp, vp, vp]
+    L.firm_stage_images.argtypes = [vp, i, vp, vp, ctypes.c_size_t]
     L.firm_cg_solve.argtypes = [vp, vp, vp, i, d, vp, ctypes.POINTER(i)]
     L.firm_toeplitz_apply.argtypes = [vp, vp, vp]
     L.firm_toeplitz_apply_static.argtypes = [i, vp, d, vp, vp, vp]
@@ -182,6 +183,10 @@ def firm_kernel(plan, M: int, R, group=None, khat_out=None):
 def firm_backproject(plan, M: int, images, shifts, R, group=None, rhs_out=None):
     _check(lib().firm_backproject(plan, M, _ptr(images), _ptr(shifts), _ptr(R), _ptr(group), _ptr(rhs_out)),
            "firm_backproject")
+
+
+def firm_stage_images(plan, M: int, images, staging, staging_bytes: int):
+    _check(lib().firm_stage_images(plan, M, _ptr(images), _ptr(staging), int(staging_bytes)), "firm_stage_images")
 
 
 def firm_cg_solve(plan, rhs, x, max_iter: int, rel_tol: float = 0.0, resid_hist=None, allow=()):

@@ -588,7 +588,14 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
     if (shifts) P.cur_shifts = stage(shifts, w.shifts, (size_t)M * 2, P.stream, e);
     else { if (e == cudaSuccess) e = cudaMemsetAsync(w.shifts, 0, sizeof(double) * 2 * (M > 0 ? M : 1), P.stream); P.cur_shifts = w.shifts; }
     FIRM_CK(e);
-    if (M > 0 && !is_device(images)) {
+    bool from_stage = false;
+    if (M > 0 && P.staged_host == images && P.staged_M == M) {
+        FIRM_CK(cudaStreamWaitEvent(P.stream, P.ev_staged, 0));     // the upload has landed
+        P.cur_images = P.staged_dev;
+        P.staged_host = nullptr;
+        P.staged_M = -1;
+        from_stage = true;
+    } else if (M > 0 && !is_device(images)) {
         FIRM_CK(cudaMemcpyAsync(w.images, images, (size_t)M * P.N * P.N * esz, cudaMemcpyHostToDevice, P.stream));
         P.cur_images = w.images;
     } else {
@@ -600,6 +607,7 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
     FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
     P.launches += M > 0 ? 1 : 0;
     FIRM_CK(launch_image_dft(P, M, P.cur_images, P.cur_shifts, P.cur_gid));
+    if (from_stage) FIRM_CK(cudaEventRecord(P.ev_stage_read, P.stream));   // staging free again
     tm.stop();
     tm.start(5);
     FIRM_CK(launch_bin(P, M, false));
@@ -614,6 +622,28 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
     if (st != FIRM_OK) return st;
     P.have_rhs = true;
     return put_out(rhs_out, w.rhs, sizeof(float) * P.N * P.N * P.N, P.stream);
+}
+
+int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging, size_t staging_bytes) {
+    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && (!images || !staging))) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    const size_t esz = P.p.img_dtype == FIRM_IMG_BF16 ? 2 : 4;
+    const size_t bytes = (size_t)M * P.N * P.N * esz;
+    if (M > 0 && (is_device(images) || !is_device(staging) || staging_bytes < bytes)) return FIRM_EINVAL;
+    if (!P.copy_stream) {
+        FIRM_CK(cudaStreamCreateWithFlags(&P.copy_stream, cudaStreamNonBlocking));
+        FIRM_CK(cudaEventCreateWithFlags(&P.ev_staged, cudaEventDisableTiming));
+        FIRM_CK(cudaEventCreateWithFlags(&P.ev_stage_read, cudaEventDisableTiming));
+    }
+    // an earlier staged upload must have been read by its image DFT (an event never
+    // recorded counts as complete)
+    FIRM_CK(cudaStreamWaitEvent(P.copy_stream, P.ev_stage_read, 0));
+    if (M > 0) FIRM_CK(cudaMemcpyAsync(staging, images, bytes, cudaMemcpyHostToDevice, P.copy_stream));
+    FIRM_CK(cudaEventRecord(P.ev_staged, P.copy_stream));
+    P.staged_host = images;
+    P.staged_dev = staging;
+    P.staged_M = M;
+    return FIRM_OK;
 }
 
 int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y) {
@@ -918,6 +948,12 @@ int firm_stage_times(firm_plan_t plan, double* out, int n) {
 
 void firm_destroy(firm_plan_t plan) {
     if (!plan) return;
+    if (plan->P.copy_stream) {
+        cudaStreamSynchronize(plan->P.copy_stream);        // a pending upload finishes first
+        cudaStreamDestroy(plan->P.copy_stream);
+        cudaEventDestroy(plan->P.ev_staged);
+        cudaEventDestroy(plan->P.ev_stage_read);
+    }
     for (int i = 0; i < Plan::kSlots; ++i) {
         if (plan->P.ev_a[i]) cudaEventDestroy(plan->P.ev_a[i]);
         if (plan->P.ev_b[i]) cudaEventDestroy(plan->P.ev_b[i]);

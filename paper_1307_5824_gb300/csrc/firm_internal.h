@@ -155,6 +155,13 @@ struct Plan {
     const int32_t* cur_gid = nullptr;
     const void* cur_images = nullptr;
     std::vector<int32_t> htab_host;
+    // images uploaded ahead of firm_backproject (firm_stage_images): copy stream,
+    // copy-done and staging-read events, and the pending upload's host pointer and M
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_staged = nullptr, ev_stage_read = nullptr;
+    const void* staged_host = nullptr;
+    const void* staged_dev = nullptr;
+    int staged_M = -1;
 };
 
 // Workspace layout (also used by firm_workspace_size with base = nullptr).

@@ -36,6 +36,15 @@ class Reconstructor:
     def backproject(self, images, shifts, R, group=None, rhs_out=None, M=None):
         L.firm_backproject(self.plan, self.M if M is None else M, images, shifts, R, group, rhs_out)
 
+    def stage_images(self, images, M=None):
+        """Starts the upload of host `images` (pinned, M x N x N) into a device buffer
+        held by this object; the next backproject with the same tensor reads it."""
+        M = self.M if M is None else M
+        if getattr(self, "_staging", None) is None:     # sized once for the plan's M
+            nbytes = max(self.M, 1) * self.N * self.N * images.element_size()
+            self._staging = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        L.firm_stage_images(self.plan, M, images, self._staging, self._staging.numel())
+
     def cg_solve(self, x, max_iter, rel_tol=0.0, rhs=None, resid_hist=None, allow=()):
         return L.firm_cg_solve(self.plan, rhs, x, max_iter, rel_tol, resid_hist, allow)
 

@@ -263,6 +263,66 @@ def test_cg_relative_tolerance_and_edge_cases(F):
     rec0.close()
 
 
+def test_staged_image_upload(F):
+    """firm_stage_images: the upload of pinned host images started ahead of firm_kernel
+    gives the same A*b as device-resident images (to the run-to-run freedom of the FP64
+    grid additions) and as the oracle; a second upload into the same staging waits for
+    the first one's image DFT; an unstaged host pointer is still copied as usual; bad
+    arguments are refused."""
+    N, M, Mp, W = 32, 77, 100, 7
+    inp = _inputs("C2", N, M)
+    K, h = _oracle_h(inp)
+    img_d = _dev(inp["images"]).to(torch.bfloat16)
+    img64 = img_d.float().cpu().numpy().astype(np.float64)
+    img_h = img_d.cpu().pin_memory()
+    img2_h = (img_d.float() * 2.0).to(torch.bfloat16).cpu().pin_memory()     # exact doubling
+    R, sh, gid = _dev(inp["R"].reshape(M, 9)), _dev(inp["shifts"]), _dev(inp["group_id"])
+    rec = F.Reconstructor(N, Mp, groups=inp["groups"], W=W, img_dtype=F._lib.FIRM_IMG_BF16)
+
+    def rhs_now():
+        out = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+        rec.copy_out(F._lib.FIRM_OUT_RHS, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    rec.backproject(img_d, sh, R, gid, M=M)
+    direct = rhs_now()
+    ref = O.backproject(img64, inp["shifts"], inp["R"], h, K)
+    assert rel(direct, ref) <= 1e-5
+    # staged, with firm_kernel running between the upload and its use
+    rec.stage_images(img_h, M=M)
+    rec.kernel(R, gid, M=M)
+    rec.backproject(img_h, sh, R, gid, M=M)
+    staged = rhs_now()
+    e = rel(staged, direct)
+    print(f"staged upload vs device images: rel diff {e:.2e}")
+    assert e <= 1e-6
+    # two uploads in a row into the same staging buffer, each read by its own call
+    rec.stage_images(img2_h, M=M)
+    rec.backproject(img2_h, sh, R, gid, M=M)
+    rec.stage_images(img_h, M=M)
+    two = rhs_now()
+    assert rel(two, 2.0 * direct) <= 1e-6
+    rec.backproject(img_h, sh, R, gid, M=M)
+    assert rel(rhs_now(), direct) <= 1e-6
+    # an upload pending for one pointer; another host pointer is copied as usual
+    rec.stage_images(img_h, M=M)
+    rec.backproject(img2_h, sh, R, gid, M=M)
+    assert rel(rhs_now(), 2.0 * direct) <= 1e-6
+    rec.backproject(img_h, sh, R, gid, M=M)
+    assert rel(rhs_now(), direct) <= 1e-6
+    # refusals
+    stg = torch.empty(M * N * N * 2, dtype=torch.uint8, device="cuda")
+    for args in ((M, img_d, stg, stg.numel()),                    # device images
+                 (Mp + 1, img_h, stg, stg.numel()),               # above the plan's M
+                 (M, img_h, stg, stg.numel() - 1),                # staging too small
+                 (M, img_h, img_h, stg.numel())):                 # staging on the host
+        with pytest.raises(F.FirmError) as ex:
+            F._lib.firm_stage_images(rec.plan, *args)
+        assert ex.value.code == F._lib.FIRM_EINVAL
+    rec.close()
+
+
 def test_bad_arguments_are_rejected(F):
     N, M = 16, 8
     rec = F.Reconstructor(N, M, W=7)
