@@ -126,17 +126,20 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
                      const double* R, const int32_t* group, float* rhs_out);
 
 /* Upload of host images ahead of firm_backproject (Section 3.4, step 1's input), so
- * that the copy overlaps firm_kernel, which does not read the images.  Starts copying
- * M host images (images: host memory, M x N x N in the plan's image type, row major;
- * page-locked for the copy to run asynchronously) into `staging` (device memory owned
- * by the caller, at least M * N * N * element-size bytes) on a copy stream of the
- * plan, and returns without waiting.  The next firm_backproject of this plan called
- * with the same host pointer and the same M orders itself after the copy and reads
- * the staged images; any other call copies as usual.  The caller keeps `images` and
- * `staging` unchanged until that firm_backproject has returned.  A later stage waits
- * for the previous staged images to be read.  firm_destroy waits for a pending copy.
- * FIRM_EINVAL: M < 0 or above the plan's M, a null pointer with M > 0, images in
- * device memory, staging not in device memory or too small. */
+ * that the copy overlaps firm_kernel, which does not read the images.  Records an
+ * upload of M host images (images: host memory, M x N x N in the plan's image type,
+ * row major; page-locked for the copy to run asynchronously) into `staging` (device
+ * memory owned by the caller, at least M * N * N * element-size bytes) and returns.
+ * The copy runs on a copy stream of the plan; it is issued by the plan's next
+ * firm_kernel once that call has queued its own small uploads (so they do not wait
+ * behind the images), or by firm_backproject if no firm_kernel comes first.  The next
+ * firm_backproject called with the same host pointer and the same M orders itself
+ * after the copy and reads the staged images; any other call copies as usual.  The
+ * caller keeps `images` and `staging` unchanged until that firm_backproject has
+ * returned.  A later upload waits for the previous staged images to be read.
+ * firm_destroy waits for a copy in flight.  FIRM_EINVAL: M < 0 or above the plan's
+ * M, a null pointer with M > 0, images in device memory, staging not in device memory
+ * or too small. */
 int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging, size_t staging_bytes);
 
 /* FIRM step 4 (Section 3.3): conjugate gradients on (A*A + lam_eff I) x = rhs from

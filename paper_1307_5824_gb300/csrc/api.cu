@@ -532,6 +532,24 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
     return FIRM_OK;
 }
 
+// Issues a recorded image upload on the copy stream, after everything queued so far on
+// the plan's stream (the calling entry point's own small uploads come first: a copy
+// engine serves queued copies in order, so poses queued behind 1.6 GB of images would
+// hold the kernel channel back for the whole upload).
+static cudaError_t start_stage(Plan& P) {
+    if (!P.staged_host || P.stage_started) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(P.ev_inputs, P.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.copy_stream, P.ev_inputs, 0);
+    // an earlier staged upload must have been read by its image DFT (an event never
+    // recorded counts as complete)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.copy_stream, P.ev_stage_read, 0);
+    if (e == cudaSuccess && P.staged_bytes > 0)
+        e = cudaMemcpyAsync(P.staged_dev, P.staged_host, P.staged_bytes, cudaMemcpyHostToDevice, P.copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(P.ev_staged, P.copy_stream);
+    if (e == cudaSuccess) P.stage_started = true;
+    return e;
+}
+
 int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, float* khat_out) {
     if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && !R)) return FIRM_EINVAL;
     Plan& P = plan->P;
@@ -542,6 +560,7 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     if (group) P.cur_gid = stage(group, w.gid, (size_t)M, P.stream, e);
     else { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
     FIRM_CK(e);
+    FIRM_CK(start_stage(P));                   // a staged image upload runs beside the kernel channel
     FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
     P.bin_M = -1;
     tm.start(0);
@@ -590,6 +609,7 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
     FIRM_CK(e);
     bool from_stage = false;
     if (M > 0 && P.staged_host == images && P.staged_M == M) {
+        FIRM_CK(start_stage(P));                                     // unless firm_kernel started it
         FIRM_CK(cudaStreamWaitEvent(P.stream, P.ev_staged, 0));     // the upload has landed
         P.cur_images = P.staged_dev;
         P.staged_host = nullptr;
@@ -632,17 +652,15 @@ int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging
     if (M > 0 && (is_device(images) || !is_device(staging) || staging_bytes < bytes)) return FIRM_EINVAL;
     if (!P.copy_stream) {
         FIRM_CK(cudaStreamCreateWithFlags(&P.copy_stream, cudaStreamNonBlocking));
+        FIRM_CK(cudaEventCreateWithFlags(&P.ev_inputs, cudaEventDisableTiming));
         FIRM_CK(cudaEventCreateWithFlags(&P.ev_staged, cudaEventDisableTiming));
         FIRM_CK(cudaEventCreateWithFlags(&P.ev_stage_read, cudaEventDisableTiming));
     }
-    // an earlier staged upload must have been read by its image DFT (an event never
-    // recorded counts as complete)
-    FIRM_CK(cudaStreamWaitEvent(P.copy_stream, P.ev_stage_read, 0));
-    if (M > 0) FIRM_CK(cudaMemcpyAsync(staging, images, bytes, cudaMemcpyHostToDevice, P.copy_stream));
-    FIRM_CK(cudaEventRecord(P.ev_staged, P.copy_stream));
     P.staged_host = images;
     P.staged_dev = staging;
+    P.staged_bytes = bytes;
     P.staged_M = M;
+    P.stage_started = false;
     return FIRM_OK;
 }
 
@@ -951,6 +969,7 @@ void firm_destroy(firm_plan_t plan) {
     if (plan->P.copy_stream) {
         cudaStreamSynchronize(plan->P.copy_stream);        // a pending upload finishes first
         cudaStreamDestroy(plan->P.copy_stream);
+        cudaEventDestroy(plan->P.ev_inputs);
         cudaEventDestroy(plan->P.ev_staged);
         cudaEventDestroy(plan->P.ev_stage_read);
     }

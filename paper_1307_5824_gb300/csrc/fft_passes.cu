@@ -642,50 +642,96 @@ __global__ void __launch_bounds__(kThreads) k_pc_z(float2* __restrict__ u, const
     block_fft_mul_ifft<L>(nl, ld, mul, st, S, tw);
 }
 
+// The preconditioner's x and y transforms, one z-plane per CTA: the plane's N x (N/2+1)
+// half spectrum stays in shared memory between the row and the column transforms, so
+// the N^3 transform is three passes (plane forward, z with the diagonal, plane
+// inverse) instead of five, and each plane is read and written once per direction.
+// All rows of the plane are one batch and all columns one batch, with up to 1024
+// threads, so a CTA has the whole plane's loads in flight at once (214 KB of shared
+// memory at N = 128).
+template <int L> __host__ __device__ constexpr int plane_threads() {
+    return L * Split<L>::L2 < 1024 ? L * Split<L>::L2 : 1024;
+}
+template <int L> __host__ __device__ constexpr int pc_plane_smem_elems() {
+    constexpr int a = smem_elems<L, false>(L), b = smem_elems<L, true>(L / 2 + 1);
+    return L * (L / 2 + 1) + (a > b ? a : b);
+}
+
+// u[z][k2][k1] = forward 2D DFT over (x, y) of plane z of r (double-word, summed to FP32)
 template <int L>
-__global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restrict__ u, const float2* __restrict__ r,
-                                                          float* __restrict__ z, double* red, CgState* cg,
-                                                          const float2* __restrict__ tw, int n_rows) {
-    // z <- P r; reduces <r, z_new> and <r, z_old> for the flexible (Polak-Ribiere)
-    // beta = (<r,z_new> - <r,z_old>) / <r_old,z_old>, which tolerates the FP32 rounding
-    // of the preconditioner apply.
+__global__ void __launch_bounds__(plane_threads<L>()) k_pc_plane_fwd(const float2* __restrict__ r,
+                                                                    float2* __restrict__ u,
+                                                                    const float2* __restrict__ tw, const CgState* cg) {
     extern __shared__ float2 S[];
-    __shared__ double s_red[2][kThreads / 32];
-    __shared__ double s_fin[2][kThreads];
+    if (cg->done) return;
+    constexpr int N = L, H = L / 2 + 1;
+    float2* plane = S;                          // [y][k1]
+    float2* X = S + N * H;                      // exchange buffer of the transforms
+    const float2* rz = r + (size_t)blockIdx.x * N * N;
+    auto ld_r = [&](int line, int n) {
+        const float2 v = __ldg(&rz[(size_t)line * N + n]);
+        return make_float2(v.x + v.y, 0.0f);
+    };
+    auto st_r = [&](int line, int k, float2 v) {
+        if (k <= N / 2) plane[line * H + k] = v;
+    };
+    block_fft<L, -1, false>(N, ld_r, st_r, X, tw);
+    float2* uz = u + (size_t)blockIdx.x * N * H;
+    auto ld_c = [&](int line, int n) { return plane[n * H + line]; };
+    auto st_c = [&](int line, int k, float2 v) { uz[(size_t)k * H + line] = v; };
+    block_fft<L, -1, true>(H, ld_c, st_c, X, tw);
+}
+
+// Plane z of the inverse 2D DFT of u (Hermitian along x) is the new z = P r; the CTA
+// also reduces <r, z_new> and <r, z_old> for the flexible (Polak-Ribiere)
+// beta = (<r,z_new> - <r,z_old>) / <r_old,z_old>, which tolerates the FP32 rounding of
+// the preconditioner apply; the last CTA forms beta (sums in CTA order).
+template <int L>
+__global__ void __launch_bounds__(plane_threads<L>()) k_pc_plane_inv(const float2* __restrict__ u,
+                                                                    const float2* __restrict__ r,
+                                                                    float* __restrict__ z, double* red, CgState* cg,
+                                                                    const float2* __restrict__ tw) {
+    extern __shared__ float2 S[];
+    __shared__ double s_red[2][32];
     __shared__ bool s_last;
     if (cg->done) return;
     constexpr int N = L, H = L / 2 + 1;
-    constexpr int ROWS = rows_per_block<L>();
-    const int r0 = blockIdx.x * ROWS;
-    const int nl = min(ROWS, n_rows - r0);
+    float2* plane = S;                          // [y][k1]
+    float2* X = S + N * H;
+    const float2* uz = u + (size_t)blockIdx.x * N * H;
+    auto ld_c = [&](int line, int n) { return uz[(size_t)n * H + line]; };
+    auto st_c = [&](int line, int k, float2 v) { plane[k * H + line] = v; };
+    block_fft<L, +1, true>(H, ld_c, st_c, X, tw);
     float2 acc = make_float2(0.0f, 0.0f), acc_old = make_float2(0.0f, 0.0f);
+    const size_t zbase = (size_t)blockIdx.x * N * N;
     auto ld = [&](int line, int n) {
-        const float2* row = u + (size_t)(r0 + line) * H;
+        const float2* row = plane + line * H;
         return n <= N / 2 ? row[n] : c_conj(row[N - n]);
     };
-    auto pre = [&](int line, int k) {       // r (double-word) and the previous z
-        const size_t i = (size_t)(r0 + line) * N + k;
+    auto pre = [&](int line, int k) {           // r (double-word) and the previous z
+        const size_t i = zbase + (size_t)line * N + k;
         const float2 ri = __ldg(&r[i]);
         return make_float3(ri.x, ri.y, z[i]);
     };
-    auto st = [&](int line, int k, float2 v, float3 rz) {
-        const float2 ri = make_float2(rz.x, rz.y);
-        acc_old = dw_acc_mul(acc_old, ri, rz.z);
-        z[(size_t)(r0 + line) * N + k] = v.x;
+    auto st = [&](int line, int k, float2 v, float3 rzv) {
+        const float2 ri = make_float2(rzv.x, rzv.y);
+        acc_old = dw_acc_mul(acc_old, ri, rzv.z);
+        z[zbase + (size_t)line * N + k] = v.x;
         acc = dw_acc_mul(acc, ri, v.x);
     };
-    fft_step1<L, +1, false>(nl, ld, S, tw);
+    fft_step1<L, +1, false>(N, ld, X, tw);
     __syncthreads();
-    fft_step2_pre<L, +1, false>(nl, pre, st, S);
+    fft_step2_pre<L, +1, false>(N, pre, st, X);
     const float2 w0 = dw_warp_sum(acc), w1 = dw_warp_sum(acc_old);
-    if ((threadIdx.x & 31) == 0) {
-        s_red[0][threadIdx.x >> 5] = dw_to_double(w0);
-        s_red[1][threadIdx.x >> 5] = dw_to_double(w1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        s_red[0][wid] = dw_to_double(w0);
+        s_red[1][wid] = dw_to_double(w1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double b0 = 0.0, b1 = 0.0;
-        for (int i = 0; i < kThreads / 32; ++i) { b0 += s_red[0][i]; b1 += s_red[1][i]; }
+        for (int i = 0; i < nw; ++i) { b0 += s_red[0][i]; b1 += s_red[1][i]; }
         red[2 * blockIdx.x] = b0;
         red[2 * blockIdx.x + 1] = b1;
         __threadfence();
@@ -693,25 +739,20 @@ __global__ void __launch_bounds__(kThreads) k_pc_rows_inv(const float2* __restri
         s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!s_last) return;
+    if (!s_last || wid != 0) return;
     __threadfence();
     double v0 = 0.0, v1 = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    for (int i = lane; i < (int)gridDim.x; i += 32) {
         v0 += ((volatile double*)red)[2 * i];
         v1 += ((volatile double*)red)[2 * i + 1];
     }
-    s_fin[0][threadIdx.x] = v0;
-    s_fin[1][threadIdx.x] = v1;
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
-            s_fin[0][threadIdx.x] += s_fin[0][threadIdx.x + s];
-            s_fin[1][threadIdx.x] += s_fin[1][threadIdx.x + s];
-        }
-        __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
     }
-    if (threadIdx.x == 0) {
-        const double rz_new = s_fin[0][0], rz_old_new_r = s_fin[1][0];
+    if (lane == 0) {
+        const double rz_new = v0, rz_old_new_r = v1;
         cg->beta = cg->first ? 0.0 : fmax(0.0, (rz_new - rz_old_new_r) / cg->rz);
         const float2 bf = dw_from_double(cg->beta);
         cg->beta_f[0] = bf.x;
@@ -730,30 +771,20 @@ template <int L>
 static cudaError_t precond_l(Plan& P, const float2* r, float* z, CgState* cg) {
     Workspace& w = P.ws;
     constexpr int N = L, H = L / 2 + 1;
-    constexpr int ROWS = rows_per_block<L>();
-    const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
+    const size_t smem_plane = sizeof(float2) * pc_plane_smem_elems<L>();
     const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(TX<L>());
     float2* u = w.t1;                       // N x N x (N/2+1) complex
     cudaError_t e;
-    PRowsFwdOp a{{}, r, u, w.tw_n, N * N, N};
-    if ((e = cudaFuncSetAttribute(k_rows_cg<L, PRowsFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+    if ((e = cudaFuncSetAttribute(k_pc_plane_fwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plane)))
         return e;
-    k_rows_cg<L, PRowsFwdOp><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(a, cg);
-    PColsYOp b{u, w.tw_n, N, H, N};
-    const int tiles = (H + TX<L>() - 1) / TX<L>();
-    if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, PColsYOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
-        return e;
-    k_cols_cg<L, -1, PColsYOp><<<N * tiles, kThreads, smem_cols, P.stream>>>(b, cg);
+    k_pc_plane_fwd<L><<<N, plane_threads<L>(), smem_plane, P.stream>>>(r, u, w.tw_n, cg);
     const int n_inner = N * H;
     if ((e = cudaFuncSetAttribute(k_pc_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols))) return e;
     k_pc_z<L><<<(n_inner + TX<L>() - 1) / TX<L>(), kThreads, smem_cols, P.stream>>>(u, w.pc_diag, w.tw_n, n_inner, cg);
-    if ((e = cudaFuncSetAttribute(k_cols_cg<L, +1, PColsYOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
+    if ((e = cudaFuncSetAttribute(k_pc_plane_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plane)))
         return e;
-    k_cols_cg<L, +1, PColsYOp><<<N * tiles, kThreads, smem_cols, P.stream>>>(b, cg);
-    if ((e = cudaFuncSetAttribute(k_pc_rows_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
-        return e;
-    k_pc_rows_inv<L><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(u, r, z, w.red_a, cg, w.tw_n, N * N);
-    P.launches += 5;
+    k_pc_plane_inv<L><<<N, plane_threads<L>(), smem_plane, P.stream>>>(u, r, z, w.red_a, cg, w.tw_n);
+    P.launches += 3;
     return cudaGetLastError();
 }
 

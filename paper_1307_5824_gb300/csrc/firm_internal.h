@@ -156,12 +156,14 @@ struct Plan {
     const void* cur_images = nullptr;
     std::vector<int32_t> htab_host;
     // images uploaded ahead of firm_backproject (firm_stage_images): copy stream,
-    // copy-done and staging-read events, and the pending upload's host pointer and M
+    // events (inputs queued, copy done, staging read), and the pending upload
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_staged = nullptr, ev_stage_read = nullptr;
+    cudaEvent_t ev_inputs = nullptr, ev_staged = nullptr, ev_stage_read = nullptr;
     const void* staged_host = nullptr;
-    const void* staged_dev = nullptr;
+    void* staged_dev = nullptr;
+    size_t staged_bytes = 0;
     int staged_M = -1;
+    bool stage_started = false;
 };
 
 // Workspace layout (also used by firm_workspace_size with base = nullptr).

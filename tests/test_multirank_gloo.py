@@ -35,11 +35,11 @@ def _worker(rank, world, port, out_path):
         rhs = O.backproject(inp["images"][a:b].astype(np.float64), inp["shifts"][a:b], inp["R"][a:b], h[a:b], K)
         t = torch.from_numpy(np.concatenate([ker.ravel(), rhs.ravel()]))
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        # timing reduction of the benchmark: max over ranks
-        ms = torch.tensor([10.0 + rank])
-        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        # timing reduction of the benchmark: max over ranks, whole job = world reconstructions
+        import bench
+        slow, per_recon = bench.job_time([10.0 + rank, 30.0 - rank], world, "cpu")
         if rank == 0:
-            np.savez(out_path, sums=t.numpy(), ms=ms.numpy())
+            np.savez(out_path, sums=t.numpy(), ms=np.array(slow), per=np.array(per_recon))
     finally:
         dist.destroy_process_group()
 
@@ -57,4 +57,5 @@ def test_image_shards_add_up_over_gloo_ranks(tmp_path, world):
     rhs = O.backproject(inp["images"].astype(np.float64), inp["shifts"], inp["R"], h, K)
     ref = np.concatenate([ker.ravel(), rhs.ravel()])
     assert np.linalg.norm(got["sums"] - ref) <= 1e-12 * np.linalg.norm(ref)
-    assert float(got["ms"][0]) == 10.0 + world - 1
+    assert list(got["ms"]) == [10.0 + world - 1, 30.0]
+    assert list(got["per"]) == [(10.0 + world - 1) / world, 30.0 / world]
