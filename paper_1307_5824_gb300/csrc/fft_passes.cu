@@ -524,6 +524,134 @@ __global__ void __launch_bounds__(kThreads) k_toep_rows_inv(TRowsInvOp op) {
     }
 }
 
+// The Toeplitz apply's x and y transforms, one z-plane per CTA (the z pass between
+// them stays a column pass): the plane's N x (N+1) half spectrum (rows of 2N padded
+// samples, k1 in [0, N]) stays in shared memory between the row and the column
+// transforms, so the intermediate never goes through L2 or HBM and the apply is three
+// launches instead of five.  Rows and columns go in the fewest batches that fit the
+// exchange buffer beside the plane in 224 KB.
+template <int L> struct TPlane {
+    static constexpr int N = L / 2, H = N + 1;
+    static constexpr int kBudget = 224 * 1024 / (int)sizeof(float2);
+    static constexpr int kPlane = N * H;
+    static constexpr int kRowElems = Split<L>::L1 * (Split<L>::L2 + 1);
+    static constexpr int rb0 = (kBudget - kPlane) / kRowElems < N ? (kBudget - kPlane) / kRowElems : N;
+    static constexpr int RB = (N + (N + rb0 - 1) / rb0 - 1) / ((N + rb0 - 1) / rb0);     // rows per batch
+    static constexpr int cb0 = (kBudget - kPlane) / L < H ? (kBudget - kPlane) / L : H;
+    static constexpr int CB = (H + (H + cb0 - 1) / cb0 - 1) / ((H + cb0 - 1) / cb0);     // columns per batch
+    static constexpr int kX = smem_elems<L, false>(RB) > smem_elems<L, true>(CB) ? smem_elems<L, false>(RB)
+                                                                                   : smem_elems<L, true>(CB);
+    static constexpr int kSmem = kPlane + kX;                                          // float2 elements
+    static constexpr int kL = Split<L>::L1 > Split<L>::L2 ? Split<L>::L1 : Split<L>::L2;
+    static constexpr int kItems = (RB > CB ? RB : CB) * kL;
+    static constexpr int kThreadsP = kItems < 1024 ? (kItems + 31) / 32 * 32 : 1024;
+};
+
+// x rows (p = r + beta p, or p = z + beta p, when CG-fused) forward into the plane,
+// then y forward (N nonzero of 2N) into t2[z][k2][k1].
+template <int L>
+__global__ void __launch_bounds__(TPlane<L>::kThreadsP) k_toep_plane_fwd(TRowsFwdOp op, float2* __restrict__ t2,
+                                                                        const CgState* cg) {
+    using T = TPlane<L>;
+    constexpr int N = T::N, H = T::H;
+    extern __shared__ float2 S[];
+    if (cg && cg->done) return;
+    float2* plane = S;                          // [y][k1]
+    float2* X = S + T::kPlane;
+    const int row0 = blockIdx.x * N;            // rows of this plane in [z][y] order
+    op.prepare();
+    for (int r0 = 0; r0 < N; r0 += T::RB) {
+        const int nl = min(T::RB, N - r0);
+        auto ld = [&](int line, int n) { return op.load(row0 + r0 + line, n); };
+        auto post = [&](int line, int n, float2 v) { op.post(row0 + r0 + line, n, v); };
+        auto st = [&](int line, int k, float2 v) {
+            if (k <= N) plane[(r0 + line) * H + k] = v;
+        };
+        fft_step1_post<L, -1, false>(nl, ld, post, X, op.tw);
+        __syncthreads();
+        fft_step2<L, -1, false>(nl, st, X);
+        __syncthreads();
+    }
+    float2* out = t2 + (size_t)blockIdx.x * 2 * N * H;
+    for (int c0 = 0; c0 < H; c0 += T::CB) {
+        const int nl = min(T::CB, H - c0);
+        auto ld = [&](int line, int n) { return n < N ? plane[n * H + c0 + line] : make_float2(0.0f, 0.0f); };
+        auto st = [&](int line, int k, float2 v) { out[(size_t)k * H + c0 + line] = v; };
+        block_fft<L, -1, true>(nl, ld, st, X, op.tw);
+    }
+}
+
+// y inverse of t2[z] keeping y < N into the plane, then the Hermitian x rows back to
+// real with the crop, 1/(2N)^3 and + lam x (op.store); CG-fused: <x, y> reduced, the
+// last CTA forms alpha (sums in CTA order).
+template <int L>
+__global__ void __launch_bounds__(TPlane<L>::kThreadsP) k_toep_plane_inv(TRowsInvOp op, const float2* __restrict__ t2) {
+    using T = TPlane<L>;
+    constexpr int N = T::N, H = T::H;
+    extern __shared__ float2 S[];
+    __shared__ double s_red[32];
+    __shared__ bool s_last;
+    if (op.cg && op.cg->done) return;
+    float2* plane = S;                          // [y][k1]
+    float2* X = S + T::kPlane;
+    const float2* in = t2 + (size_t)blockIdx.x * 2 * N * H;
+    for (int c0 = 0; c0 < H; c0 += T::CB) {
+        const int nl = min(T::CB, H - c0);
+        auto ld = [&](int line, int n) { return __ldg(&in[(size_t)n * H + c0 + line]); };
+        auto st = [&](int line, int k, float2 v) {
+            if (k < N) plane[k * H + c0 + line] = v;
+        };
+        block_fft<L, +1, true>(nl, ld, st, X, op.tw);
+    }
+    float2 acc = make_float2(0.0f, 0.0f);
+    op.prepare();
+    op.acc = &acc;
+    const int row0 = blockIdx.x * N;
+    for (int r0 = 0; r0 < N; r0 += T::RB) {
+        const int nl = min(T::RB, N - r0);
+        auto ld = [&](int line, int n) {
+            const float2* row = plane + (r0 + line) * H;
+            return n <= N ? row[n] : c_conj(row[2 * N - n]);
+        };
+        auto pre = [&](int line, int k) { return op.pre(row0 + r0 + line, k); };
+        auto st = [&](int line, int k, float2 v, float xv) { op.store(row0 + r0 + line, k, v, xv); };
+        fft_step1<L, +1, false>(nl, ld, X, op.tw);
+        __syncthreads();
+        fft_step2_pre<L, +1, false>(nl, pre, st, X);
+        __syncthreads();
+    }
+    if (!op.cg) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const float2 wsum = dw_warp_sum(acc);
+    if (lane == 0) s_red[wid] = dw_to_double(wsum);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < nw; ++i) b += s_red[i];
+        op.red[blockIdx.x] = b;
+        __threadfence();
+        const unsigned t = atomicAdd(&op.cg->ticket_a, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last || wid != 0) return;
+    __threadfence();
+    double v = 0.0;
+    for (int i = lane; i < (int)gridDim.x; i += 32) v += ((volatile double*)op.red)[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+        const double pq = v;
+        const double alpha = (op.cg->use_pc ? op.cg->rz : op.cg->rr) / pq;
+        op.cg->pq = pq;
+        op.cg->alpha = alpha;
+        const float2 af = dw_from_double(isfinite(alpha) ? alpha : 0.0);
+        op.cg->alpha_f[0] = af.x;
+        op.cg->alpha_f[1] = af.y;
+        op.cg->ticket_a = 0;
+    }
+}
+
 template <int L, class Op>
 __global__ void __launch_bounds__(kThreads) k_rows_cg(Op op, const CgState* cg) {
     extern __shared__ float2 S[];
@@ -556,39 +684,29 @@ __global__ void __launch_bounds__(kThreads) k_cols_cg(const Op op, const CgState
 template <int L>
 static cudaError_t toeplitz_l(Plan& P, const float* x, float* y, const float2* cg_r, CgState* cg,
                               const float* cg_z) {
+    using T = TPlane<L>;
     Workspace& w = P.ws;
     const int N = P.N;
-    constexpr int ROWS = rows_per_block<L>();
-    const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
+    const size_t smem_plane = sizeof(float2) * T::kSmem;
     const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(TX<L>());
     cudaError_t e;
-    // pass 1: rows of x (or p = r + beta p), forward, half spectrum
-    TRowsFwdOp a{{}, x, cg ? const_cast<float*>(x) : nullptr, cg_r, cg, w.t1, w.tw_2n, N * N, N, cg_z};
-    if ((e = cudaFuncSetAttribute(k_rows_cg<L, TRowsFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+    // pass 1: per z-plane, rows of x (or p = r + beta p) forward, then y forward
+    TRowsFwdOp a{{}, x, cg ? const_cast<float*>(x) : nullptr, cg_r, cg, nullptr, w.tw_2n, N * N, N, cg_z};
+    if ((e = cudaFuncSetAttribute(k_toep_plane_fwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plane)))
         return e;
-    k_rows_cg<L, TRowsFwdOp><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(a, cg);
-    // pass 2: y forward (N nonzero of 2N)
-    TColsYFwdOp b{w.t1, w.t2, w.tw_2n, N, N + 1, N};
-    if ((e = cudaFuncSetAttribute(k_cols_cg<L, -1, TColsYFwdOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
-        return e;
-    const int tiles_b = (N + 1 + TX<L>() - 1) / TX<L>();
-    k_cols_cg<L, -1, TColsYFwdOp><<<N * tiles_b, kThreads, smem_cols, P.stream>>>(b, cg);
-    // pass 3: z forward x K-hat x z inverse
+    k_toep_plane_fwd<L><<<N, T::kThreadsP, smem_plane, P.stream>>>(a, w.t2, cg);
+    // pass 2: z forward x K-hat x z inverse
     const int n_inner = 2 * N * (N + 1);
     if ((e = cudaFuncSetAttribute(k_toep_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols))) return e;
     k_toep_z<L><<<(n_inner + TX<L>() - 1) / TX<L>(), kThreads, smem_cols, P.stream>>>(w.t2, w.khat, w.tw_2n, n_inner, N, cg);
-    // pass 4: y inverse, keep y < N
-    TColsYInvOp d{w.t2, w.t1, w.tw_2n, N, N + 1, N};
-    if ((e = cudaFuncSetAttribute(k_cols_cg<L, +1, TColsYInvOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
-        return e;
-    k_cols_cg<L, +1, TColsYInvOp><<<N * tiles_b, kThreads, smem_cols, P.stream>>>(d, cg);
-    // pass 5: rows inverse (Hermitian), crop, scale, + lam x, <x, y>
+    // pass 3: per z-plane, y inverse (keep y < N), rows inverse (Hermitian), crop,
+    // scale, + lam x, <x, y>
     const float scale = 1.0f / ((float)L * (float)L * (float)L);
-    TRowsInvOp f{w.t1, x, y, w.red_a, cg, w.tw_2n, N * N, N, scale, 0.0f, w.lam, nullptr};
-    if ((e = cudaFuncSetAttribute(k_toep_rows_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+    TRowsInvOp f{nullptr, x, y, w.red_a, cg, w.tw_2n, N * N, N, scale, 0.0f, w.lam, nullptr};
+    if ((e = cudaFuncSetAttribute(k_toep_plane_inv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plane)))
         return e;
-    k_toep_rows_inv<L><<<(N * N + ROWS - 1) / ROWS, kThreads, smem_rows, P.stream>>>(f);
-    P.launches += 5;
+    k_toep_plane_inv<L><<<N, T::kThreadsP, smem_plane, P.stream>>>(f, w.t2);
+    P.launches += 3;
     return cudaGetLastError();
 }
 
