@@ -555,11 +555,11 @@ def main():
     except Exception:
         hbm_peak, hbm_src = 6800.0, "fallback"
     # a7 alone: Toeplitz applies on device buffers, CUDA events on the plan's stream.
-    # Algorithmic bytes of one apply (five passes): x rows in + t1 out, t1 -> t2 (y),
-    # t2 + K-hat -> t2 (z), t2 -> t1 (y inverse), t1 + x -> y.
-    H = N * N * (N + 1) * 8
-    toep_bytes = (N ** 3 * 4 + H) + (H + 2 * H) + (2 * H + 2 * N * 2 * N * (N + 1) * 4 + 2 * H) + (2 * H + H) \
-        + (H + 2 * N ** 3 * 4)
+    # Algorithmic bytes of one apply (three passes; the x/y intermediate of each plane
+    # stays on chip): x in + t2 out, t2 + K-hat -> t2 (z), t2 + x in -> y out, with
+    # t2 = N x 2N x (N+1) complex64.
+    T2 = N * 2 * N * (N + 1) * 8
+    toep_bytes = (N ** 3 * 4 + T2) + (2 * T2 + 2 * N * 2 * N * (N + 1) * 4) + (T2 + 2 * N ** 3 * 4)
     xa = torch.randn((N, N, N), device=dev)
     ya = torch.empty_like(xa)
     for _ in range(3):
@@ -576,6 +576,23 @@ def main():
     toeplitz = {"applies_per_s": 1.0 / toep_s, "us_per_apply": toep_s * 1e6, "algorithmic_bytes": toep_bytes,
                 "achieved_gbs": toep_bytes / toep_s / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": toep_bytes / toep_s / 1e9 / hbm_peak, "peak_source": hbm_src}
+
+    # the forward projector A of the solution (type-2 NUFFT at every half-disc sample)
+    # and the data term |b - A x|^2 / |b|^2, device buffers, CUDA events
+    fwd_out = torch.empty((M, (nK + 1) // 2, 2), dtype=torch.float32, device=dev)
+    rec.forward(x, R, gid, fwd_out)
+    torch.cuda.synchronize(dev)
+    t0e.record(stream)
+    rec.forward(x, R, gid, fwd_out)
+    t1e.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_s = t0e.elapsed_time(t1e) / 1e3
+    t0r = time.perf_counter()
+    res2, b2 = rec.data_residual(x, img, sh, R, gid)
+    res_s = time.perf_counter() - t0r
+    del fwd_out
+    forward = {"ms": fwd_s * 1e3, "points": M * ((nK + 1) // 2), "gpts_per_s": M * ((nK + 1) // 2) / fwd_s / 1e9,
+               "data_residual_ms": res_s * 1e3, "data_term_rel": res2 / b2}
 
     cpu = None
     if not args.no_cpu:
@@ -599,6 +616,7 @@ def main():
         "spread_points": pts,
         "toeplitz_applies_per_s": toeplitz["applies_per_s"],
         "toeplitz": toeplitz,
+        "forward_projector": forward,
         "cg_iters_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
         "cg_iters": iters,
         "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},

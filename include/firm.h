@@ -125,6 +125,32 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
 int firm_backproject(firm_plan_t plan, int M, const void* images, const double* shifts,
                      const double* R, const int32_t* group, float* rhs_out);
 
+/* Forward projector A (Section 3.1, eq. forward-projector; with eq. truncation's disc):
+ *     (A V)_m(k) = h_m(|w_k|) sum_n V_n exp(-i <n, xi_{m,k}>),  xi = R_m^T (2 pi k / N, 0),
+ * for the half disc of every image (the order of FIRM_OUT_SAMPLES: (0, k2) for
+ * k2 = 0..N/2, then k1 = 1..N/2 with every k2 of the disc; the other half is the
+ * complex conjugate for a real V).  Computed as a type-2 NUFFT: V divided by the
+ * window's transform, zero-padded to the (2N)^3 fine grid, transformed, and
+ * interpolated with the same Kaiser-Bessel window at each slice point.  V: N^3
+ * float32 (host or device).  out: M x |K|/2 complex float32 (interleaved re, im; host
+ * or device).  group may be NULL (group 0).  Uses the fine grid and the binning
+ * buffers of the plan (its kept Ker, K-hat and A*b are not touched).  FIRM_EINVAL:
+ * M < 0 or above the plan's M, or a null pointer with M > 0. */
+int firm_forward(firm_plan_t plan, int M, const float* V, const double* R, const int32_t* group, float* out);
+
+/* Data term of the reconstruction (Section 3.3: the least-squares residual the
+ * solution minimises, used for the L-curve of Section 3.3): with b_m(k) the centred
+ * DFT of image m with its shift phase (eq. measurement, as firm_backproject takes it)
+ * and A the forward projector above, out2[0] = sum over m and the whole disc K of
+ * |b_m(k) - (A V)_m(k)|^2 and out2[1] = sum of |b_m(k)|^2, both in FP64 (the half
+ * disc counted twice except k = 0).  Sums go through one FP64 partial per binning
+ * work item (no floating-point atomics); the points' order within the binning varies
+ * between calls, so repeated calls agree to FP64 rounding.  Arguments as firm_backproject
+ * plus V (N^3 float32, host or device); out2: 2 doubles (host or device).  M = 0
+ * gives zeros.  FIRM_EINVAL as firm_forward, or out2 NULL. */
+int firm_data_residual(firm_plan_t plan, int M, const float* V, const void* images, const double* shifts,
+                       const double* R, const int32_t* group, double* out2);
+
 /* Upload of host images ahead of firm_backproject (Section 3.4, step 1's input), so
  * that the copy overlaps firm_kernel, which does not read the images.  Records an
  * upload of M host images (images: host memory, M x N x N in the plan's image type,

@@ -24,6 +24,7 @@ FIRM_FLAG_FP64_CG = 1
 
 EXPORTED = [
     "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_stage_images", "firm_cg_solve",
+    "firm_forward", "firm_data_residual",
     "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_set_precond", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
     "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_target", "firm_pc_axis",
     "firm_set_precond_table", "firm_pc_bin_volumes", "firm_pc_baseline", "firm_pc_residual_target", "firm_set_precond_residual",
@@ -77,6 +78,8 @@ def lib() -> ctypes.CDLL:
     L.firm_kernel.argtypes = [vp, i, vp, vp, vp]
     L.firm_backproject.argtypes = [vp, i, vp, vp, vp, vp, vp]
     L.firm_stage_images.argtypes = [vp, i, vp, vp, ctypes.c_size_t]
+    L.firm_forward.argtypes = [vp, i, vp, vp, vp, vp]
+    L.firm_data_residual.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
     L.firm_cg_solve.argtypes = [vp, vp, vp, i, d, vp, ctypes.POINTER(i)]
     L.firm_toeplitz_apply.argtypes = [vp, vp, vp]
     L.firm_toeplitz_apply_static.argtypes = [i, vp, d, vp, vp, vp]
@@ -187,6 +190,25 @@ def firm_backproject(plan, M: int, images, shifts, R, group=None, rhs_out=None):
 
 def firm_stage_images(plan, M: int, images, staging, staging_bytes: int):
     _check(lib().firm_stage_images(plan, M, _ptr(images), _ptr(staging), int(staging_bytes)), "firm_stage_images")
+
+
+def disc_size(N: int) -> int:
+    """|K|, the number of integer frequencies with |k| <= N/2 (sizes the sample arrays)."""
+    h = N // 2
+    k = np.arange(-h, h + 1)
+    return int(((k[:, None] ** 2 + k[None, :] ** 2) <= h * h).sum())
+
+
+def firm_forward(plan, M: int, V, R, group, out):
+    _check(lib().firm_forward(plan, M, _ptr(V), _ptr(R), _ptr(group), _ptr(out)), "firm_forward")
+
+
+def firm_data_residual(plan, M: int, V, images, shifts, R, group=None):
+    """(sum |b - A V|^2, sum |b|^2) over every image's whole disc."""
+    out = np.zeros(2, np.float64)
+    _check(lib().firm_data_residual(plan, M, _ptr(V), _ptr(images), _ptr(shifts), _ptr(R), _ptr(group), _ptr(out)),
+           "firm_data_residual")
+    return float(out[0]), float(out[1])
 
 
 def firm_cg_solve(plan, rhs, x, max_iter: int, rel_tol: float = 0.0, resid_hist=None, allow=()):

@@ -169,6 +169,7 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.count = c.take<uint32_t>(nb3);
     w.cursor = c.take<uint32_t>(nb3);
     w.work = c.take<int4>(max_work);
+    w.item_part = c.take<double>(2 * max_work);
     w.counters = c.take<int>(8);
     const size_t grid_bytes = std::max(Gk * Gk * Gk * sizeof(double), Gr * Gr * Gr * 2 * sizeof(double));
     w.grid = c.take<double>(grid_bytes / sizeof(double));
@@ -662,6 +663,76 @@ int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging
     P.staged_M = M;
     P.stage_started = false;
     return FIRM_OK;
+}
+
+// Poses, groups and the volume of a forward-projector call staged on the plan's stream.
+static cudaError_t stage_forward_inputs(Plan& P, int M, const float* V, const double* R, const int32_t* group,
+                                        const float*& Vd) {
+    Workspace& w = P.ws;
+    cudaError_t e = cudaSuccess;
+    P.cur_R = stage(R, w.R, (size_t)M * 9, P.stream, e);
+    if (group) P.cur_gid = stage(group, w.gid, (size_t)M, P.stream, e);
+    else if (e == cudaSuccess) { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
+    Vd = stage(V, w.q, (size_t)P.N * P.N * P.N, P.stream, e);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream);
+    P.bin_M = -1;
+    return e;
+}
+
+int firm_forward(firm_plan_t plan, int M, const float* V, const double* R, const int32_t* group, float* out) {
+    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !V || !out))) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    Workspace& w = P.ws;
+    if (M == 0) return FIRM_OK;
+    const float* Vd = nullptr;
+    FIRM_CK(stage_forward_inputs(P, M, V, R, group, Vd));
+    FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
+    P.launches += 1;
+    FIRM_CK(launch_bin(P, M, false));
+    float2* ghat = reinterpret_cast<float2*>(w.grid);
+    FIRM_CK(launch_fwd_transform(P, Vd, ghat));
+    const bool odev = is_device(out);
+    float2* od = odev ? reinterpret_cast<float2*>(out) : w.samples;
+    FIRM_CK(launch_interp(P, M, ghat, od, nullptr, nullptr));
+    const int st = check_spread_flag(P);
+    if (st != FIRM_OK) return st;
+    if (!odev) return put_out(out, od, sizeof(float2) * (size_t)M * P.nH, P.stream);
+    return FIRM_OK;
+}
+
+int firm_data_residual(firm_plan_t plan, int M, const float* V, const void* images, const double* shifts,
+                       const double* R, const int32_t* group, double* out2) {
+    if (!plan || !out2 || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !V || !images))) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    Workspace& w = P.ws;
+    if (M == 0) {
+        const double z[2] = {0.0, 0.0};
+        if (is_device(out2)) FIRM_CK(cudaMemcpyAsync(out2, z, sizeof(z), cudaMemcpyHostToDevice, P.stream));
+        else { out2[0] = 0.0; out2[1] = 0.0; }
+        return FIRM_OK;
+    }
+    const float* Vd = nullptr;
+    FIRM_CK(stage_forward_inputs(P, M, V, R, group, Vd));
+    cudaError_t e = cudaSuccess;
+    const double* sh = shifts ? stage(shifts, w.shifts, (size_t)M * 2, P.stream, e) : nullptr;
+    FIRM_CK(e);
+    if (!shifts) { FIRM_CK(cudaMemsetAsync(w.shifts, 0, sizeof(double) * 2 * M, P.stream)); sh = w.shifts; }
+    const size_t esz = P.p.img_dtype == FIRM_IMG_BF16 ? 2 : 4;
+    const void* img = images;
+    if (!is_device(images)) {
+        FIRM_CK(cudaMemcpyAsync(w.images, images, (size_t)M * P.N * P.N * esz, cudaMemcpyHostToDevice, P.stream));
+        img = w.images;
+    }
+    FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
+    P.launches += 1;
+    FIRM_CK(launch_image_dft(P, M, img, sh, P.cur_gid, true));    // b itself into samples
+    FIRM_CK(launch_bin(P, M, false));                                // b copied in scatter order
+    float2* ghat = reinterpret_cast<float2*>(w.grid);
+    FIRM_CK(launch_fwd_transform(P, Vd, ghat));
+    FIRM_CK(launch_interp(P, M, ghat, nullptr, w.item_part, w.red_a));
+    const int st = check_spread_flag(P);
+    if (st != FIRM_OK) return st;
+    return put_out(out2, w.red_a, 2 * sizeof(double), P.stream);
 }
 
 int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y) {

@@ -289,11 +289,73 @@ cudaError_t launch_rhs_transform(Plan& P) {
 }
 
 // ---------------------------------------------------------------------------
+// Forward projector (eq. forward-projector), transform half of the type-2 NUFFT: the
+// volume times (-1)^n / phihat(n / 2N) per axis (dec_r; the sign centres the fine
+// grid so that a slice point's fine-grid coordinate indexes it directly), zero-padded
+// to (2N)^3 at n mod 2N and transformed forward along x, y, z in place.
+// ---------------------------------------------------------------------------
+struct FwdRowsOp : NoFinish {
+    const float* V; const float* dec; float2* g; const float2* tw; int n_rows, G, N;
+    __device__ __forceinline__ float2 load(int row, int n) const {      // row = i3 * N + i2
+        const int h = N / 2;
+        const int n1 = n < h ? n : (n >= G - h ? n - G : G);
+        if (n1 == G) return make_float2(0.0f, 0.0f);
+        const int i1 = n1 + h, i2 = row % N, i3 = row / N;
+        const float v = __ldg(&V[(size_t)row * N + i1]) * __ldg(&dec[i1]) * __ldg(&dec[i2]) * __ldg(&dec[i3]);
+        return make_float2(v, 0.0f);
+    }
+    __device__ __forceinline__ void store(int row, int k, float2 v) const {
+        const int h = N / 2, i2 = row % N, i3 = row / N;
+        const int j2 = i2 < h ? i2 - h + G : i2 - h, j3 = i3 < h ? i3 - h + G : i3 - h;
+        g[((size_t)j3 * G + j2) * G + k] = v;
+    }
+};
+struct FwdColsYOp {            // planes o = i3 (j3 = n3 mod G), columns j1
+    float2* g; const float2* tw; int n_outer, n_inner, G, N;
+    __device__ __forceinline__ size_t plane(int o) const {
+        const int h = N / 2;
+        return (size_t)(o < h ? o - h + G : o - h) * G * G;
+    }
+    __device__ __forceinline__ float2 load(int o, int n, int i) const {
+        const int h = N / 2;
+        if (n >= h && n < G - h) return make_float2(0.0f, 0.0f);          // padding rows
+        return g[plane(o) + (size_t)n * G + i];
+    }
+    __device__ __forceinline__ void store(int o, int k, int i, float2 v) const { g[plane(o) + (size_t)k * G + i] = v; }
+};
+struct FwdColsZOp {            // columns (j2, j1) of all G^2
+    float2* g; const float2* tw; int n_outer, n_inner, G, N;
+    __device__ __forceinline__ float2 load(int, int n, int i) const {
+        const int h = N / 2;
+        if (n >= h && n < G - h) return make_float2(0.0f, 0.0f);          // padding planes
+        return g[(size_t)n * n_inner + i];
+    }
+    __device__ __forceinline__ void store(int, int k, int i, float2 v) const { g[(size_t)k * n_inner + i] = v; }
+};
+
+cudaError_t launch_fwd_transform(Plan& P, const float* V, float2* ghat) {
+    Workspace& w = P.ws;
+    const int N = P.N, G = P.Gr;
+    cudaError_t e = cudaSuccess;
+    FwdRowsOp a{{}, V, w.dec_r, ghat, w.tw_2n, N * N, G, N};
+    FwdColsYOp b{ghat, w.tw_2n, N, G, G, N};
+    FwdColsZOp c{ghat, w.tw_2n, 1, G * G, G, N};
+    FIRM_SWITCH_2N(G, {
+        if ((e = run_rows<LL, -1>(a, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, -1>(b, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, -1>(c, P.stream)) != cudaSuccess) return e;
+    });
+    P.launches += 3;
+    return e;
+}
+
+// ---------------------------------------------------------------------------
 // Image DFT (FIRM step 1)
 // ---------------------------------------------------------------------------
 struct ImgArgs {
     const void* images; const double* shifts; const int32_t* gid; const int32_t* htab;
     const float* h1; float2* samples; const float2* tw; int nH, n_ctf;
+    int plain;              // 1: b itself (no h, k = 0 not halved), for the data residual
 };
 
 template <int N, class T>
@@ -340,9 +402,9 @@ __global__ void __launch_bounds__(kThreads) k_image_dft(const ImgArgs a) {
         const int kk = __ldg(&a.htab[t]);
         const int k1 = (int16_t)(kk & 0xffff), k2 = kk >> 16;
         float2 v = S1[((k2 + N) % N) * H1 + k1];
-        float hs = __ldg(&a.h1[(size_t)g * a.nH + t]);
+        float hs = a.plain ? 1.0f : __ldg(&a.h1[(size_t)g * a.nH + t]);
         if ((k1 + k2) & 1) hs = -hs;
-        if (t == 0) hs *= 0.5f;
+        if (t == 0 && !a.plain) hs *= 0.5f;
         float sn, cs;
         sincospif((float)k1 * s1 + (float)k2 * s2, &sn, &cs);
         const float2 ph = make_float2(cs * hs, sn * hs);
@@ -360,9 +422,10 @@ static cudaError_t image_dft_n(Plan& P, int M, const ImgArgs& a) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* shifts, const int32_t* gid) {
+cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* shifts, const int32_t* gid,
+                             bool plain) {
     if (M <= 0) return cudaSuccess;
-    ImgArgs a{images, shifts, gid, P.ws.htab, P.ws.h1, P.ws.samples, P.ws.tw_n, P.nH, P.n_ctf};
+    ImgArgs a{images, shifts, gid, P.ws.htab, P.ws.h1, P.ws.samples, P.ws.tw_n, P.nH, P.n_ctf, plain ? 1 : 0};
     const bool bf = P.p.img_dtype == FIRM_IMG_BF16;
     switch (P.N) {
         case 16: return bf ? image_dft_n<16, uint16_t>(P, M, a) : image_dft_n<16, float>(P, M, a);

@@ -84,6 +84,7 @@ struct Workspace {
     float2* samples_b = nullptr;    // A*b weights in scatter order (written by the scatter pass)
     uint16_t* perm = nullptr;       // per payload position: index in scatter order within its piece
     int4* work = nullptr;           // (brick, start, count, -)
+    double* item_part = nullptr;    // per work item: two FP64 partial sums (data residual)
     int* counters = nullptr;        // [0] work items, [1] work cursor, [2] error flag
     double* grid = nullptr;         // fine grid, FP64 (real for Ker, complex for A*b)
     float2* fx1 = nullptr;          // FFT intermediates
@@ -192,7 +193,16 @@ cudaError_t launch_spread_batch(int n, bool kernel_channel, int W, const KbPoly&
 
 // ---- launchers (fft_passes.cu) ----
 cudaError_t fft_init_constants();
-cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* shifts, const int32_t* gid);
+// plain: b itself (no CTF weight, k = 0 not halved) instead of the A*b weights
+cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* shifts, const int32_t* gid,
+                             bool plain = false);
+// Forward projector (type-2 NUFFT): the deconvolved, centred, zero-padded volume
+// transformed forward on the (2N)^3 grid (ghat, G^3 complex), then interpolated at
+// the A*b channel's binned points.  Forward mode (item_part == nullptr): out[m][t] =
+// h_m(k_t) (A V)(xi_mt).  Residual mode: per work item sums of c |b - h A V|^2 and
+// c |b|^2 into item_part, then their item-order sums into sums[0..1] (device).
+cudaError_t launch_fwd_transform(Plan& P, const float* V, float2* ghat);
+cudaError_t launch_interp(Plan& P, int M, const float2* ghat, float2* out, double* item_part, double* sums);
 cudaError_t launch_ker_transform(Plan& P);     // grid -> Ker half box
 cudaError_t launch_khat(Plan& P);              // Ker -> K-hat
 cudaError_t launch_rhs_transform(Plan& P);     // grid -> A*b

@@ -805,4 +805,215 @@ cudaError_t launch_spread_batch(int n, bool kc, int W, const KbPoly& poly, const
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Interpolation (the forward projector's type-2 NUFFT, the transpose of spreading):
+// (A V)(xi) = sum over the W^3 cells j around the point of phi(j - y) g[j], g the
+// forward-transformed, deconvolved volume on the centred 2N grid.  Per work item (one
+// 8^3 brick of the A*b binning) the brick's (8+W)^3 region of g is staged in shared
+// memory (real and imaginary planes; the bank-class order of the piece keeps a warp's
+// lanes on distinct banks) and each thread gathers its points' taps.  Forward mode
+// writes h_m(k) (A V) at [m][t]; residual mode reads b (the unweighted image DFT in
+// scatter order) and sums c |b - h A V|^2 and c |b|^2 per work item (c = 2 off the
+// origin: the other half of the disc is the complex conjugate).
+// ---------------------------------------------------------------------------
+struct InterpArgs {
+    const uint32_t* payload;
+    const int4* work;
+    int* counters;
+    const ImgGeom* geom;
+    const int32_t* htab;
+    const int32_t* gid;
+    const float* h1;          // [group][t] h
+    const float2* ghat;       // G^3 complex, [j3][j2][j1] on the centred grid
+    const float2* samples_b;  // residual mode: b in scatter order
+    const uint16_t* perm;
+    float2* out;              // forward mode: [m][t]
+    double* item_part;        // residual mode: per work item (sum c|r|^2, sum c|b|^2)
+    int G, halfG, nb, nH, n_ctf;
+    float scale;
+    KbPoly poly;
+};
+
+template <int W, bool RESID>
+__global__ void __launch_bounds__(kSpreadThreads) k_interp(const InterpArgs a) {
+    constexpr int BZ = kBrick;
+    constexpr int RG = kBrick + W;
+    constexpr int RG3 = RG * RG * (BZ + W);
+    extern __shared__ float s_f[];
+    float* s_re = s_f;
+    float* s_im = s_f + RG3;
+    __shared__ int s_item;
+    __shared__ double s_red[2][kSpreadWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n_work = a.counters[0];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[1], 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_work) break;
+        const int4 wk = a.work[item];
+        const int b = wk.x;
+        const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
+        const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * BZ;
+        const int o0 = lo0 - W / 2, o1 = lo1 - W / 2, o2 = lo2 - W / 2;
+        for (int i = threadIdx.x; i < RG3; i += blockDim.x) {
+            const int rx = i % RG, ry = (i / RG) % RG, rz = i / (RG * RG);
+            int gx = o0 + rx, gy = o1 + ry, gz = o2 + rz;
+            gx += (gx < 0) ? a.G : 0;
+            gx -= (gx >= a.G) ? a.G : 0;
+            gy += (gy < 0) ? a.G : 0;
+            gy -= (gy >= a.G) ? a.G : 0;
+            gz += (gz < 0) ? a.G : 0;
+            gz -= (gz >= a.G) ? a.G : 0;
+            const float2 v = __ldg(&a.ghat[((size_t)gz * a.G + gy) * a.G + gx]);
+            s_re[i] = v.x;
+            s_im[i] = v.y;
+        }
+        __syncthreads();
+        double acc_r = 0.0, acc_b = 0.0;
+        for (int i = threadIdx.x; i < wk.z; i += blockDim.x) {
+            const uint32_t pos = (uint32_t)wk.y + i;
+            const uint32_t id = __ldg(&a.payload[pos]);
+            const int m = (int)(id >> kTBits);
+            const int t = (int)(id & ((1u << kTBits) - 1u));
+            const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
+            const int base = region_base<W, BZ>(p, lo0, lo1, lo2);
+            if (base < 0) {
+                atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never read
+                continue;
+            }
+            float wx[W], wy[W], wz[W];
+            window_taps<W>(a.poly, p.f[0], wx);
+            window_taps<W>(a.poly, p.f[1], wy);
+            window_taps<W>(a.poly, p.f[2], wz);
+            float fr = 0.0f, fi = 0.0f;
+#pragma unroll
+            for (int dz = 0; dz < W; ++dz) {
+#pragma unroll
+                for (int dy = 0; dy < W; ++dy) {
+                    const int row = base + (dz * RG + dy) * RG;
+                    float rr = 0.0f, ri = 0.0f;
+#pragma unroll
+                    for (int dx = 0; dx < W; ++dx) {
+                        rr = fmaf(wx[dx], s_re[row + dx], rr);
+                        ri = fmaf(wx[dx], s_im[row + dx], ri);
+                    }
+                    const float wyz = wz[dz] * wy[dy];
+                    fr = fmaf(wyz, rr, fr);
+                    fi = fmaf(wyz, ri, fi);
+                }
+            }
+            const int g = a.gid ? min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1) : 0;
+            const float h = __ldg(&a.h1[(size_t)g * a.nH + t]);
+            if (!RESID) {
+                a.out[(size_t)m * a.nH + t] = make_float2(h * fr, h * fi);
+            } else {
+                const float2 bv = __ldg(&a.samples_b[wk.y + __ldg(&a.perm[pos])]);
+                const double dr = (double)bv.x - (double)h * fr, di = (double)bv.y - (double)h * fi;
+                const double c = t == 0 ? 1.0 : 2.0;
+                acc_r += c * (dr * dr + di * di);
+                acc_b += c * ((double)bv.x * bv.x + (double)bv.y * bv.y);
+            }
+        }
+        if (RESID) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc_r += __shfl_xor_sync(0xffffffffu, acc_r, o);
+                acc_b += __shfl_xor_sync(0xffffffffu, acc_b, o);
+            }
+            if (lane == 0) {
+                s_red[0][warp] = acc_r;
+                s_red[1][warp] = acc_b;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double r = 0.0, bb = 0.0;
+                for (int w = 0; w < kSpreadWarps; ++w) { r += s_red[0][w]; bb += s_red[1][w]; }
+                a.item_part[2 * item] = r;
+                a.item_part[2 * item + 1] = bb;
+            }
+        }
+    }
+}
+
+// out[0..1] = sums over the work items, in item order (one CTA: fixed order).
+__global__ void __launch_bounds__(1024) k_item_sum(const double* __restrict__ part, const int* __restrict__ counters,
+                                                   double* __restrict__ out) {
+    __shared__ double s[2][1024];
+    const int n = counters[0];
+    double r = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        r += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    s[0][threadIdx.x] = r;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + k];
+            s[1][threadIdx.x] += s[1][threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = s[0][0];
+        out[1] = s[1][0];
+    }
+}
+
+template <int W, bool RESID>
+static cudaError_t interp_w(Plan& P, const InterpArgs& a) {
+    constexpr int RG3 = (kBrick + W) * (kBrick + W) * (kBrick + W);
+    const size_t smem = sizeof(float) * 2 * RG3;
+    cudaError_t e = cudaFuncSetAttribute(k_interp<W, RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp<W, RESID>, kSpreadThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    k_interp<W, RESID><<<P.num_sms * per_sm, kSpreadThreads, smem, P.stream>>>(a);
+    P.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp(Plan& P, int M, const float2* ghat, float2* out, double* item_part, double* sums) {
+    if (M <= 0) return cudaSuccess;
+    Workspace& w = P.ws;
+    InterpArgs a;
+    a.payload = w.payload;
+    a.work = w.work;
+    a.counters = w.counters;
+    a.geom = w.geom;
+    a.htab = w.htab;
+    a.gid = P.cur_gid;
+    a.h1 = w.h1;
+    a.ghat = ghat;
+    a.samples_b = w.samples_b;
+    a.perm = w.perm;
+    a.out = out;
+    a.item_part = item_part;
+    a.G = P.Gr;
+    a.halfG = P.Gr / 2;
+    a.nb = P.nbr;
+    a.nH = P.nH;
+    a.n_ctf = P.n_ctf;
+    a.scale = (float)(P.Gr / P.N);
+    a.poly = P.poly;
+    const bool resid = item_part != nullptr;
+    cudaError_t e;
+    switch (P.p.W) {
+        case 6: e = resid ? interp_w<6, true>(P, a) : interp_w<6, false>(P, a); break;
+        case 7: e = resid ? interp_w<7, true>(P, a) : interp_w<7, false>(P, a); break;
+        case 8: e = resid ? interp_w<8, true>(P, a) : interp_w<8, false>(P, a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess || !resid) return e;
+    k_item_sum<<<1, 1024, 0, P.stream>>>(item_part, w.counters, sums);
+    P.launches += 1;
+    return cudaGetLastError();
+}
+
 }  // namespace firm

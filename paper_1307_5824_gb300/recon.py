@@ -45,6 +45,20 @@ class Reconstructor:
             self._staging = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         L.firm_stage_images(self.plan, M, images, self._staging, self._staging.numel())
 
+    def forward(self, V, R, group=None, out=None, M=None):
+        """(A V) on every image's half disc, M x |K|/2 complex64 (out: a device or host
+        float32 array of shape (M, |K|/2, 2), allocated on the device when None)."""
+        M = self.M if M is None else M
+        if out is None:
+            nH = (L.disc_size(self.N) + 1) // 2
+            out = torch.empty((M, nH, 2), dtype=torch.float32, device=self.device)
+        L.firm_forward(self.plan, M, V, R, group, out)
+        return out
+
+    def data_residual(self, V, images, shifts, R, group=None, M=None):
+        """(sum |b - A V|^2, sum |b|^2) over every image's whole disc, FP64."""
+        return L.firm_data_residual(self.plan, self.M if M is None else M, V, images, shifts, R, group)
+
     def cg_solve(self, x, max_iter, rel_tol=0.0, rhs=None, resid_hist=None, allow=()):
         return L.firm_cg_solve(self.plan, rhs, x, max_iter, rel_tol, resid_hist, allow)
 
