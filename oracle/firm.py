@@ -35,7 +35,7 @@ __all__ = [
     "disc", "electron_wavelength_A", "ctf", "ctf_weights", "slice_points",
     "forward", "adjoint", "kernel", "kernel_at", "adjoint_at", "image_dft",
     "backproject", "backproject_at", "circulant_column", "khat", "khat_half",
-    "toeplitz_direct", "toeplitz_apply", "lambda_eff", "cg", "wrapped_spectrum",
+    "toeplitz_direct", "toeplitz_apply", "gradient_penalty", "lambda_eff", "cg", "wrapped_spectrum",
     "circulant_preconditioner", "sums_at_voxels",
 ]
 
@@ -316,6 +316,21 @@ def toeplitz_apply(Khat: np.ndarray, V: np.ndarray, lam_eff: float = 0.0) -> np.
     pad[:N, :N, :N] = V
     y = np.fft.ifftn(Khat * np.fft.fftn(pad))[:N, :N, :N]
     return y + lam_eff * V
+
+
+def gradient_penalty(V: np.ndarray) -> np.ndarray:
+    """D^T D V for the first differences D of V on its box with zero outside: the
+    gradient of ||D V||^2 / 2, a Fourier-domain damping of high frequencies (Section 5
+    names damping high frequencies as a regulariser that fits FIRM; reading: the
+    first-difference penalty).  Per axis a and voxel n: 2 V_n - V_{n+e_a} - V_{n-e_a},
+    with V = 0 outside the box, summed over the three axes."""
+    P = np.pad(np.asarray(V), 1)
+    c = P[1:-1, 1:-1, 1:-1]
+    out = 6.0 * c
+    out = out - P[2:, 1:-1, 1:-1] - P[:-2, 1:-1, 1:-1]
+    out = out - P[1:-1, 2:, 1:-1] - P[1:-1, :-2, 1:-1]
+    out = out - P[1:-1, 1:-1, 2:] - P[1:-1, 1:-1, :-2]
+    return out
 
 
 def lambda_eff(lam: float, mode: int, ker0: float) -> float:

@@ -625,3 +625,42 @@ def test_bin_volumes_partition_the_grid_and_baseline_of_uniform_density():
     assert np.allclose(v * N ** 3, cnt)
     b = LP.baseline(v, v, 1e-3)
     assert np.allclose(b[v > 0], -np.log(1.001))
+
+
+# -- high-frequency damping (first-difference penalty) ------------------------------
+def _stencil_ker(N):
+    """The penalty as a convolution kernel on [-N, N)^3: 6 at lag 0, -1 at lags +-e_a."""
+    K = np.zeros((2 * N,) * 3)
+    K[N, N, N] = 6.0
+    for a in range(3):
+        for s in (-1, 1):
+            idx = [N, N, N]
+            idx[a] += s
+            K[tuple(idx)] = -1.0
+    return K
+
+
+def test_gradient_penalty_is_the_first_difference_quadratic_form():
+    """<V, D^T D V> = sum over the three axes of the squared first differences of V
+    padded with zeros (each boundary edge to the zero exterior counted once)."""
+    rng = np.random.default_rng(61)
+    V = rng.standard_normal((5, 6, 7))
+    q = sum(float((np.diff(np.pad(V, 1), axis=a)[tuple(slice(1, -1) if b != a else slice(None)
+                                                      for b in range(3))] ** 2).sum()) for a in range(3))
+    assert np.isclose(np.vdot(V, O.gradient_penalty(V)).real, q, rtol=1e-13)
+
+
+def test_gradient_penalty_is_a_toeplitz_convolution_with_the_stencil():
+    """D^T D V = (stencil * V) by the direct Toeplitz sum, and through the 2N circulant,
+    whose spectrum is 6 - 2 sum_a cos(pi j_a / N) (the closed form the GPU adds to K-hat)."""
+    N = 4
+    rng = np.random.default_rng(62)
+    V = rng.standard_normal((N, N, N))
+    Ks = _stencil_ker(N)
+    assert np.allclose(O.toeplitz_direct(Ks, V).real, O.gradient_penalty(V), atol=1e-12)
+    Kh = O.khat(Ks)
+    j = np.arange(2 * N)
+    c = np.cos(np.pi * j / N)
+    sym = 6.0 - 2.0 * (c[:, None, None] + c[None, :, None] + c[None, None, :])
+    assert np.allclose(Kh.real, sym, atol=1e-12) and np.abs(Kh.imag).max() < 1e-12
+    assert np.allclose(O.toeplitz_apply(Kh, V).real, O.gradient_penalty(V), atol=1e-12)
