@@ -180,6 +180,19 @@ int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging
 int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, double rel_tol,
                   double* resid_hist, int* iters_out);
 
+/* High-frequency damping (Section 5: FIRM can take regularisers that are natural in
+ * Fourier space, damping high frequencies among them; the paper gives no formula, and
+ * this reading is the first-difference penalty).  From the next firm_kernel on, the
+ * system solved by firm_cg_solve (and applied by firm_toeplitz_apply) is
+ *     (A*A + mu_eff D^T D + lam_eff I) V = A*b,
+ * D the first differences of V along x, y, z on its box (V = 0 outside), i.e. the
+ * kernel Ker gains the 7-point stencil 6 delta(n) - sum of delta(n -+ e_a); it is added
+ * to K-hat (spectrum 6 - 2 sum_a cos(pi j_a / N) on the 2N grid), so a CG iteration
+ * costs the same.  mu_eff = mu * Ker(0) under FIRM_LAMBDA_RELATIVE, mu under
+ * FIRM_LAMBDA_ABSOLUTE.  K-hat-based preconditioners see the damped spectrum.
+ * mu = 0 (the default) switches it off.  FIRM_EINVAL: mu < 0 or not finite. */
+int firm_set_damping(firm_plan_t plan, double mu);
+
 /* Preconditioner used by firm_cg_solve from its next call on (north star; the paper's
  * CG is unpreconditioned).  FIRM_PRECOND_NONE: plain CG (Section 3.3).
  * FIRM_PRECOND_CIRCULANT: z = F^-1 diag(1 / (kappa(k) + lam_eff)) F r on the N^3 grid,

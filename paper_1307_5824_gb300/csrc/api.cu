@@ -579,6 +579,7 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     FIRM_CK(launch_khat(P));
     FIRM_CK(launch_lam_eff(P));
     if (P.p.flags & FIRM_FLAG_FP64_CG) FIRM_CK(launch_khat64(P));
+    FIRM_CK(launch_damping(P));
     tm.stop();
     // lam_eff from Ker(0) (the n = 0 entry of the half box), also kept on the host
     float ker0 = 0.f;
@@ -733,6 +734,12 @@ int firm_data_residual(firm_plan_t plan, int M, const float* V, const void* imag
     const int st = check_spread_flag(P);
     if (st != FIRM_OK) return st;
     return put_out(out2, w.red_a, 2 * sizeof(double), P.stream);
+}
+
+int firm_set_damping(firm_plan_t plan, double mu) {
+    if (!plan || !(mu >= 0.0) || !std::isfinite(mu)) return FIRM_EINVAL;
+    plan->P.mu = mu;
+    return FIRM_OK;
 }
 
 int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y) {

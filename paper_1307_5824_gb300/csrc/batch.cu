@@ -108,6 +108,7 @@ cudaError_t plan_middle(Plan& P, const firm_batch_item& it, bool spread_here) {
     BCK(launch_ker_transform(P));
     BCK(launch_khat(P));
     BCK(launch_lam_eff(P));
+    BCK(launch_damping(P));
     BCK(launch_image_dft(P, M, P.cur_images, P.cur_shifts, P.cur_gid));
     BCK(launch_bin(P, M, false));
     BCK(launch_spread_clear(P, false));

@@ -234,6 +234,43 @@ cudaError_t launch_lam_eff(Plan& P) {
     return cudaGetLastError();
 }
 
+// High-frequency damping mu ||D V||^2 (D: first differences of V on its box, zero
+// outside; a Fourier-domain regulariser of the kind Section 5 says FIRM takes in
+// naturally).  D^T D is the convolution with the 7-point stencil 6 delta(n) -
+// sum over a and +-1 of delta(n -+ e_a), whose support lies well inside [-N, N)^3, so it
+// is added to the circulant's spectrum on the 2N grid and costs nothing per CG
+// iteration: K-hat(j) += mu_eff (6 - 2 sum_a cos(pi j_a / N)), mu_eff = mu Ker(0)
+// (relative reading, as lam_eff) or mu.  khat: half spectrum [j3][j2][j1], j1 in
+// [0, N]; khat64 (FP64 CG mode, may be null): the full (2N)^3.
+__global__ void k_khat_damp(float* __restrict__ khat, double* __restrict__ khat64, int N, double mu, int relative,
+                            const float* __restrict__ lam) {
+    const double m = relative ? mu * (double)lam[1] : mu;
+    const long long G = 2LL * N, H = N + 1;
+    const long long n_half = G * G * H, n_full = khat64 ? G * G * G : 0;
+    const long long total = n_half > n_full ? n_half : n_full;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        if (i < n_half) {
+            const int j1 = (int)(i % H), j2 = (int)((i / H) % G), j3 = (int)(i / (H * G));
+            const double sym = 6.0 - 2.0 * (cospi((double)j1 / N) + cospi((double)j2 / N) + cospi((double)j3 / N));
+            khat[i] += (float)(m * sym);
+        }
+        if (i < n_full) {
+            const int j1 = (int)(i % G), j2 = (int)((i / G) % G), j3 = (int)(i / (G * G));
+            const double sym = 6.0 - 2.0 * (cospi((double)j1 / N) + cospi((double)j2 / N) + cospi((double)j3 / N));
+            khat64[i] += m * sym;
+        }
+    }
+}
+
+cudaError_t launch_damping(Plan& P) {
+    if (!(P.mu > 0.0)) return cudaSuccess;
+    const bool fp64 = (P.p.flags & FIRM_FLAG_FP64_CG) != 0;
+    k_khat_damp<<<P.num_sms * 4, 256, 0, P.stream>>>(P.ws.khat, fp64 ? P.ws.khat64 : nullptr, P.N, P.mu,
+                                                     P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? 1 : 0, P.ws.lam);
+    P.launches += 1;
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // A*b: 2N^3 complex FP64 grid -> N^3 real
 // ---------------------------------------------------------------------------

@@ -133,6 +133,7 @@ struct Plan {
     int chunk = kChunk;             // points per spreading work item (kMinChunk..kChunk)
     KbPoly poly{};
     double lam_eff = 0.0;
+    double mu = 0.0;                // high-frequency damping weight (firm_set_damping)
     float h2_max = 1.0f;           // largest kernel-channel weight (bounds the fixed-point scale)
     bool have_kernel = false, have_rhs = false;
     bool timing = false;
@@ -228,6 +229,7 @@ cudaError_t launch_pc_from_table(Plan& P, const float* table);
 
 // ---- launchers (cg64.cu): the FP64 CG mode ----
 cudaError_t launch_khat64(Plan& P);                 // khat64 from the Ker half box
+cudaError_t launch_damping(Plan& P);                // mu D^T D added to K-hat (and khat64); no-op at mu = 0
 // CG from x0 = 0 (first_iter == 0 queues the initialisation), then n_iter iterations.
 cudaError_t launch_cg64(Plan& P, const float* rhs, int max_iter, double rel_tol, int first_iter, int n_iter);
 cudaError_t launch_cg64_result(Plan& P);            // x64 -> ws.x (float)

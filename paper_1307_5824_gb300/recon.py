@@ -65,6 +65,10 @@ class Reconstructor:
     def toeplitz_apply(self, x, y):
         L.firm_toeplitz_apply(self.plan, x, y)
 
+    def set_damping(self, mu: float):
+        """mu of the first-difference penalty mu ||D V||^2, from the next kernel() on."""
+        L.firm_set_damping(self.plan, mu)
+
     def set_precond(self, mode: int):
         L.firm_set_precond(self.plan, mode)
 
