@@ -35,7 +35,7 @@ __all__ = [
     "disc", "electron_wavelength_A", "ctf", "ctf_weights", "slice_points",
     "forward", "adjoint", "kernel", "kernel_at", "adjoint_at", "image_dft",
     "backproject", "backproject_at", "circulant_column", "khat", "khat_half",
-    "toeplitz_direct", "toeplitz_apply", "gradient_penalty", "lambda_eff", "cg", "wrapped_spectrum",
+    "toeplitz_direct", "toeplitz_apply", "gradient_penalty", "lambda_eff", "cg", "projected_cg", "wrapped_spectrum",
     "circulant_preconditioner", "sums_at_voxels",
 ]
 
@@ -370,6 +370,69 @@ def cg(apply, rhs: np.ndarray, max_iter: int, rel_tol: float = 0.0, x0=None, pre
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, np.array(hist), it
+
+
+def projected_cg(apply, rhs: np.ndarray, max_iter: int, rel_tol: float = 0.0):
+    """Positivity-constrained FIRM solve (Section 5 names positivity constraints as prior
+    knowledge FIRM can take in; reading: the quadratic of Section 3.3,
+    min 1/2 <x, H x> - <rhs, x> over x >= 0 with H = apply, SPD), by conjugate
+    gradients on the free variables with projection and restarts (Polyak's method for
+    bound-constrained quadratics, a published method), in float64:
+
+      restart: free = {x > 0 or r > 0} (r = rhs - H x), p = r on free, 0 elsewhere;
+      step:    q = H p, alpha = <r_f, r_f> / <p, q>; the largest feasible step is
+               amax = min over p_i < 0 of x_i / -p_i;
+               if amax < alpha: x += amax p, r -= amax q, the blocking variables set to
+               0 (x projected onto x >= 0), restart;
+               else x += alpha p, r -= alpha q; if ||r_f|| <= rel_tol ||rhs||: stop when
+               no bound variable has r_i > 0, else restart; otherwise
+               p = r_f + (<r_f, r_f>_new / <r_f, r_f>) p.
+
+    Every step costs one apply; stops after max_iter applies.  Returns (x, applies,
+    converged)."""
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    bnorm = float(np.linalg.norm(rhs))
+    its = 0
+    restart = True
+    free = p = None
+    rz = 0.0
+    while True:
+        if restart:
+            free = (x > 0) | (r > 0)
+            rf = np.where(free, r, 0.0)
+            rz = float(np.vdot(rf, rf))
+            if np.sqrt(rz) <= rel_tol * bnorm:
+                return x, its, True
+            p = rf
+            restart = False
+        if its >= max_iter:
+            return x, its, False
+        q = apply(p)
+        its += 1
+        alpha = rz / float(np.vdot(p, q))
+        neg = p < 0
+        ratio = np.full(x.shape, np.inf)
+        ratio[neg] = x[neg] / -p[neg]
+        amax = float(ratio.min())
+        if amax < alpha:
+            x = x + amax * p
+            r = r - amax * q
+            x[neg & (ratio <= amax)] = 0.0        # the blocking variables
+            x = np.maximum(x, 0.0)
+            restart = True
+            continue
+        x = x + alpha * p
+        r = r - alpha * q
+        rf = np.where(free, r, 0.0)
+        rz_new = float(np.vdot(rf, rf))
+        if np.sqrt(rz_new) <= rel_tol * bnorm:
+            if not np.any(~free & (r > 0)):
+                return x, its, True
+            restart = True
+            continue
+        p = rf + (rz_new / rz) * p
+        rz = rz_new
 
 
 # ----------------------------------------------------------------------------

@@ -664,3 +664,54 @@ def test_gradient_penalty_is_a_toeplitz_convolution_with_the_stencil():
     sym = 6.0 - 2.0 * (c[:, None, None] + c[None, :, None] + c[None, None, :])
     assert np.allclose(Kh.real, sym, atol=1e-12) and np.abs(Kh.imag).max() < 1e-12
     assert np.allclose(O.toeplitz_apply(Kh, V).real, O.gradient_penalty(V), atol=1e-12)
+
+
+# -- positivity: projected CG (Polyak) ------------------------------------------------
+def _explicit_system(N=4, lam=0.05, seed=71):
+    """H = explicit matrix of (Ker * .) + lam I for a small random image set (columns by
+    the direct Toeplitz sum), SPD."""
+    inp = synth.config_inputs("C2", M=12, N=N)
+    K = O.disc(N)
+    h = O.ctf_weights(N, K, inp["groups"], inp["group_id"])
+    Ker = O.kernel(inp["R"], h, K, N).real
+    n = N ** 3
+    H = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        H[:, j] = O.toeplitz_direct(Ker, e.reshape(N, N, N)).real.ravel()
+    H = 0.5 * (H + H.T) + lam * Ker[N, N, N] * np.eye(n)
+    return H
+
+
+def test_projected_cg_equals_nonnegative_least_squares():
+    """With H = C^T C (Cholesky), min 1/2 x^T H x - b^T x over x >= 0 is the NNLS problem
+    min ||C x - C^-T b|| (scipy.optimize.nnls, Lawson-Hanson); the constraint binds."""
+    from scipy.optimize import nnls
+    H = _explicit_system()
+    n = H.shape[0]
+    rng = np.random.default_rng(72)
+    b = rng.standard_normal(n) * np.abs(H).max()
+    C = np.linalg.cholesky(H).T
+    d = np.linalg.solve(C.T, b)
+    ref, _ = nnls(C, d, maxiter=50 * n)
+    x, its, ok = O.projected_cg(lambda v: (H @ v.ravel()).reshape(v.shape), b.reshape(4, 4, 4), 5000, 1e-13)
+    assert ok and (ref == 0).sum() > 5                      # several bounds active
+    assert np.linalg.norm(x.ravel() - ref) <= 1e-9 * np.linalg.norm(ref)
+    # KKT: x >= 0, gradient >= 0 on the bound set, ~0 on the free set
+    g = H @ x.ravel() - b
+    assert x.min() >= 0
+    assert g[x.ravel() == 0].min() >= -1e-9 * np.abs(b).max()
+    assert np.abs(g[x.ravel() > 0]).max() <= 1e-9 * np.abs(b).max()
+
+
+def test_projected_cg_is_cg_when_the_solution_is_positive():
+    H = _explicit_system()
+    n = H.shape[0]
+    xt = 1.0 + np.random.default_rng(73).random(n)        # strictly positive solution
+    b = H @ xt
+    apply = lambda v: (H @ v.ravel()).reshape(v.shape)
+    x, its, ok = O.projected_cg(apply, b.reshape(4, 4, 4), 500, 1e-12)
+    assert ok and np.linalg.norm(x.ravel() - xt) <= 1e-9 * np.linalg.norm(xt)
+    xc, _, _ = O.cg(apply, b.reshape(4, 4, 4), its)
+    assert np.linalg.norm(x - xc) <= 1e-9 * np.linalg.norm(xc)   # no bound ever hit: the same iterates
