@@ -594,6 +594,17 @@ def main():
     forward = {"ms": fwd_s * 1e3, "points": M * ((nK + 1) // 2), "gpts_per_s": M * ((nK + 1) // 2) / fwd_s / 1e9,
                "data_residual_ms": res_s * 1e3, "data_term_rel": res2 / b2}
 
+    # the positivity-constrained solve (projected CG), capped at 200 applies: its rate
+    # with the host's two scalar reads per step (A*b and K-hat of the last step)
+    rec.backproject(img, sh, R, gid)
+    xn = torch.empty_like(x)
+    torch.cuda.synchronize(dev)
+    t0n = time.perf_counter()
+    st_n, its_n = rec.solve_nonneg(xn, 200, 1e-4, allow=(L.FIRM_ENOTCONV,))
+    nn_s = time.perf_counter() - t0n
+    nonneg = {"applies": its_n, "ms": nn_s * 1e3, "us_per_apply": nn_s / max(its_n, 1) * 1e6,
+              "held_at_zero_frac": float((xn == 0).float().mean()), "converged": st_n == L.FIRM_OK}
+
     cpu = None
     if not args.no_cpu:
         est, sample, parts = oracle_sample(inp, iters)
@@ -617,6 +628,7 @@ def main():
         "toeplitz_applies_per_s": toeplitz["applies_per_s"],
         "toeplitz": toeplitz,
         "forward_projector": forward,
+        "nonneg_solve": nonneg,
         "cg_iters_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
         "cg_iters": iters,
         "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},

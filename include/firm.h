@@ -180,6 +180,23 @@ int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging
 int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, double rel_tol,
                   double* resid_hist, int* iters_out);
 
+/* Positivity constraint (Section 5 names positivity among the prior knowledge FIRM can
+ * take in; the paper gives no method, and this reading is the quadratic of Section 3.3
+ * restricted to V >= 0):
+ *     min 1/2 <V, H V> - <A*b, V>  subject to V >= 0,  H = A*A + lam_eff I (+ the damping),
+ * solved from V = 0 by conjugate gradients on the free voxels with projection and
+ * restarts (Polyak's method for bound-constrained quadratics: a step is capped where a
+ * voxel would cross zero, the blocking voxels are set to 0 and CG restarts; a voxel held
+ * at 0 is released when its residual turns positive).  Uses the plan's A*b and K-hat
+ * (firm_backproject and firm_kernel first).  Stops when the residual on the free voxels
+ * is <= rel_tol ||A*b|| and no voxel held at 0 has a positive residual (the KKT
+ * conditions), or after max_iter Toeplitz applies (FIRM_ENOTCONV; x then holds the last
+ * feasible iterate).  x: N^3 float32 (host or device), x >= 0 on return.  *iters_out
+ * (nullable): Toeplitz applies.  The host reads two scalars per step.  FIRM_ESTATE:
+ * no K-hat or A*b yet; FIRM_EINVAL: x NULL, max_iter < 0, rel_tol < 0 or not finite;
+ * FIRM_EBREAKDOWN: <p, H p> <= 0. */
+int firm_solve_nonneg(firm_plan_t plan, float* x, int max_iter, double rel_tol, int* iters_out);
+
 /* High-frequency damping (Section 5: FIRM can take regularisers that are natural in
  * Fourier space, damping high frequencies among them; the paper gives no formula, and
  * this reading is the first-difference penalty).  From the next firm_kernel on, the

@@ -24,7 +24,7 @@ FIRM_FLAG_FP64_CG = 1
 
 EXPORTED = [
     "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_stage_images", "firm_cg_solve",
-    "firm_forward", "firm_data_residual", "firm_set_damping",
+    "firm_forward", "firm_data_residual", "firm_set_damping", "firm_solve_nonneg",
     "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_set_precond", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
     "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_target", "firm_pc_axis",
     "firm_set_precond_table", "firm_pc_bin_volumes", "firm_pc_baseline", "firm_pc_residual_target", "firm_set_precond_residual",
@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
     L.firm_stage_images.argtypes = [vp, i, vp, vp, ctypes.c_size_t]
     L.firm_forward.argtypes = [vp, i, vp, vp, vp, vp]
     L.firm_set_damping.argtypes = [vp, d]
+    L.firm_solve_nonneg.argtypes = [vp, vp, i, d, ctypes.POINTER(i)]
     L.firm_data_residual.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
     L.firm_cg_solve.argtypes = [vp, vp, vp, i, d, vp, ctypes.POINTER(i)]
     L.firm_toeplitz_apply.argtypes = [vp, vp, vp]
@@ -198,6 +199,15 @@ def disc_size(N: int) -> int:
     h = N // 2
     k = np.arange(-h, h + 1)
     return int(((k[:, None] ** 2 + k[None, :] ** 2) <= h * h).sum())
+
+
+def firm_solve_nonneg(plan, x, max_iter: int, rel_tol: float, allow=()):
+    """Returns (status, Toeplitz applies).  Raises unless the status is OK or in `allow`."""
+    it = ctypes.c_int(0)
+    st = lib().firm_solve_nonneg(plan, _ptr(x), int(max_iter), float(rel_tol), ctypes.byref(it))
+    if st != FIRM_OK and st not in allow:
+        _check(st, "firm_solve_nonneg")
+    return st, it.value
 
 
 def firm_set_damping(plan, mu: float):

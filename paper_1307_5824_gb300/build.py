@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfirm.so")
-SOURCES = ["api.cu", "spread.cu", "fft_passes.cu", "cg.cu", "cg64.cu", "lpre.cu", "batch.cu"]
+SOURCES = ["api.cu", "spread.cu", "fft_passes.cu", "cg.cu", "cg64.cu", "lpre.cu", "batch.cu", "poscg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", os.path.join(os.path.dirname(HERE), "include")]

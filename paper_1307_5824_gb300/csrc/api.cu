@@ -736,6 +736,21 @@ int firm_data_residual(firm_plan_t plan, int M, const float* V, const void* imag
     return put_out(out2, w.red_a, 2 * sizeof(double), P.stream);
 }
 
+int firm_solve_nonneg(firm_plan_t plan, float* x, int max_iter, double rel_tol, int* iters_out) {
+    if (!plan || !x || max_iter < 0 || !(rel_tol >= 0.0) || !std::isfinite(rel_tol)) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!P.have_kernel || !P.have_rhs) return FIRM_ESTATE;
+    const bool xdev = is_device(x);
+    float* xd = xdev ? x : P.ws.x;
+    const int st = pos_solve(P, xd, max_iter, rel_tol, iters_out);
+    if (st == FIRM_ECUDA) return st;
+    if (!xdev) {
+        const int s2 = put_out(x, xd, sizeof(float) * P.N * P.N * P.N, P.stream);
+        if (s2 != FIRM_OK) return s2;
+    }
+    return st;
+}
+
 int firm_set_damping(firm_plan_t plan, double mu) {
     if (!plan || !(mu >= 0.0) || !std::isfinite(mu)) return FIRM_EINVAL;
     plan->P.mu = mu;

@@ -230,6 +230,9 @@ cudaError_t launch_pc_from_table(Plan& P, const float* table);
 // ---- launchers (cg64.cu): the FP64 CG mode ----
 cudaError_t launch_khat64(Plan& P);                 // khat64 from the Ker half box
 cudaError_t launch_damping(Plan& P);                // mu D^T D added to K-hat (and khat64); no-op at mu = 0
+// Positivity-constrained solve (poscg.cu) on the plan's A*b and K-hat; x: device N^3.
+// Returns a firm_status (FIRM_ENOTCONV at max_iter).
+int pos_solve(Plan& P, float* x, int max_iter, double rel_tol, int* iters_out);
 // CG from x0 = 0 (first_iter == 0 queues the initialisation), then n_iter iterations.
 cudaError_t launch_cg64(Plan& P, const float* rhs, int max_iter, double rel_tol, int first_iter, int n_iter);
 cudaError_t launch_cg64_result(Plan& P);            // x64 -> ws.x (float)

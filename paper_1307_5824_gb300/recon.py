@@ -65,6 +65,10 @@ class Reconstructor:
     def toeplitz_apply(self, x, y):
         L.firm_toeplitz_apply(self.plan, x, y)
 
+    def solve_nonneg(self, x, max_iter, rel_tol, allow=()):
+        """V >= 0 minimiser of the data term (projected CG); returns (status, applies)."""
+        return L.firm_solve_nonneg(self.plan, x, max_iter, rel_tol, allow)
+
     def set_damping(self, mu: float):
         """mu of the first-difference penalty mu ||D V||^2, from the next kernel() on."""
         L.firm_set_damping(self.plan, mu)

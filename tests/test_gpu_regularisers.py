@@ -119,3 +119,50 @@ def test_damping_off_restores_the_spectrum_and_bad_values_are_refused(F):
         with pytest.raises(F.FirmError):
             rec.set_damping(bad)
     rec.close()
+
+
+def test_nonnegative_solve_matches_oracle_and_meets_kkt(F):
+    """firm_solve_nonneg (projected CG, Polyak) against the oracle's projected CG run to a
+    tight tolerance: both reach the unique minimiser of the strictly convex quadratic over
+    V >= 0 (lam = 1e-2 keeps the system's condition number near 100, so FP32 residuals of
+    1e-5 bound the volume's error near 1e-3).  The GPU result meets the KKT conditions
+    (checked in FP64 with the oracle's operator), and the constraint binds on this data."""
+    N, M, W, lam = 16, 37, 7, 1e-2
+    inp, Ker, rhs = _problem(N, M)
+    ker0 = Ker[N, N, N]
+    Kh = O.khat(Ker).real
+
+    def apply(v):
+        return O.toeplitz_apply(Kh, v, lam * ker0).real
+
+    xo, its_o, ok = O.projected_cg(apply, rhs, 20000, 1e-10)
+    assert ok
+    rec = F.Reconstructor(N, M, groups=inp["groups"], W=W, lam=lam)
+    x = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    with pytest.raises(F.FirmError) as e:
+        rec.solve_nonneg(x, 10, 1e-5)                   # no K-hat, no A*b yet
+    assert e.value.code == F._lib.FIRM_ESTATE
+    R, gid = _dev(inp["R"].reshape(M, 9)), _dev(inp["group_id"])
+    rec.kernel(R, gid)
+    rec.backproject(_dev(inp["images"]), _dev(inp["shifts"]), R, gid)
+    st, its = rec.solve_nonneg(x, 5000, 1e-5)
+    xg = x.cpu().numpy().astype(np.float64)
+    e = rel(xg, xo)
+    held = int((xg == 0).sum())
+    print(f"non-negative solve: {its} applies (oracle {its_o}), rel err {e:.2e}, {held} voxels held at 0")
+    assert st == 0 and xg.min() >= 0.0 and held > 50
+    assert e <= 2e-3
+    g = apply(xg) - rhs                                 # gradient of the quadratic
+    scale = np.abs(rhs).max()
+    assert g[xg == 0].min() >= -1e-3 * scale            # held voxels: the gradient points outward
+    assert np.linalg.norm(g[xg > 0]) <= 1e-3 * np.linalg.norm(rhs)
+    # host output, and refusals
+    xh = np.empty((N, N, N), np.float32)
+    st2, its2 = F._lib.firm_solve_nonneg(rec.plan, xh, 5000, 1e-5)
+    assert st2 == 0 and rel(xh, xg) <= 1e-5
+    for bad in ((-1, 1e-5), (10, -1.0), (10, float("nan"))):
+        with pytest.raises(F.FirmError):
+            rec.solve_nonneg(x, *bad)
+    st3, its3 = rec.solve_nonneg(x, 3, 1e-5, allow=(F._lib.FIRM_ENOTCONV,))
+    assert st3 == F._lib.FIRM_ENOTCONV and its3 == 3 and float(x.min()) >= 0.0
+    rec.close()
