@@ -69,9 +69,11 @@ def parse():
                     help="training kernels use 1..this many of the defocus values (max 20)")
     ap.add_argument("--train-defocus", type=int, default=8, help="defocus values (1.0-3.5 um) training draws from")
     ap.add_argument("--train-lr-final", type=float, default=None, help="final Adam step size (cosine decay from 1e-3)")
-    ap.add_argument("--workload", default="C3", choices=["C3", "C5", "C4"],
+    ap.add_argument("--workload", default="C3", choices=["C3", "C5", "C4", "RCT"],
                     help="C3: 50k Haar views, 20 groups; C5: 40k views 85%% in a 15 degree cap, 8 groups; "
-                         "C4: 64 independent reconstructions, N in {48,64,80,96}, 1k-8k images, 25 CG iterations")
+                         "C4: 64 independent reconstructions, N in {48,64,80,96}, 1k-8k images, 25 CG iterations; "
+                         "RCT: random conical tilt (60 degrees), N=96, 10k images, SNR 1, with the FCR of the "
+                         "solution inside and outside the missing cone")
     ap.add_argument("--batch", type=int, default=None, help="C4: reconstructions per batch (default 64)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -140,6 +142,17 @@ def workload(M_override=None, N_override=None, name=WORKLOAD):
     import synth
     inp = synth.config_inputs(name, M=M_override, N=N_override)
     return inp
+
+
+def workload_name(inp, W, precond, name):
+    """The workload as a sentence, from its configuration."""
+    c, N, M = inp["cfg"], inp["N"], inp["M"]
+    views = {"haar": "Haar views", "cap": "views 85% in a 15-degree cap", "mixed": "vMF/Haar views",
+             "rct": "random conical tilt %g deg" % c.get("tilt_deg", 0.0)}[c["views"]]
+    groups = "%d defocus groups" % len(c["defocus_um"]) if c["defocus_um"] else "no CTF"
+    return ("N=%d volume, %d BF16 %dx%d images (%d-blob phantom, %s, %s, SNR %g), KB W=%d sigma=2, "
+            "lambda=1e-3 x Ker(0), %s-preconditioned CG to rel-res 1e-4"
+            % (N, M, N, N, c["n_blobs"], views, groups, c["snr"], W, precond))
 
 
 def disc_size(N):
@@ -605,6 +618,21 @@ def main():
     nonneg = {"applies": its_n, "ms": nn_s * 1e3, "us_per_apply": nn_s / max(its_n, 1) * 1e6,
               "held_at_zero_frac": float((xn == 0).float().mean()), "converged": st_n == L.FIRM_OK}
 
+    # random conical tilt: resolution of the solution against the phantom inside and
+    # outside the missing cone (Section 4's modified FCR)
+    fcr = None
+    if args.workload == "RCT":
+        import synth
+        from paper_1307_5824_gb300 import metrics as Mt
+        truth = synth.blob_volume(inp["blobs"], N)
+        sol = x.cpu().numpy()
+        cone = Mt.cone_mask(N, (0, 0, 1), 90.0 - inp["cfg"]["tilt_deg"])
+        f_out, f_in = Mt.fsc(sol, truth, ~cone), Mt.fsc(sol, truth, cone)
+        below = np.flatnonzero(f_out < 0.5)
+        fcr = {"cone_half_angle_deg": 90.0 - inp["cfg"]["tilt_deg"],
+               "outside": [round(float(v), 4) for v in f_out], "inside": [round(float(v), 4) for v in f_in],
+               "first_shell_outside_below_0.5": int(below[0]) + 1 if below.size else None}
+
     cpu = None
     if not args.no_cpu:
         est, sample, parts = oracle_sample(inp, iters)
@@ -615,9 +643,7 @@ def main():
         "metric": METRIC, "value": ms_per_recon / 1e3, "unit": "s/recon", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "N=128 volume, 50000 BF16 128x128 images (60-blob phantom, Haar views, "
-                               "20 defocus groups, SNR 0.05), KB W=%d sigma=2, lambda=1e-3 x Ker(0), "
-                               "%s-preconditioned CG to rel-res 1e-4" % (W, args.precond),
+        "config": {"workload": workload_name(inp, W, args.precond, args.workload),
                    "N": N, "M": M, "W": W, "precond": args.precond,
                    "l2": "inputs larger than L2: 1.64 GB BF16 images read and a 1.07 GB FP64 fine grid "
                          "written every step"},
@@ -629,6 +655,7 @@ def main():
         "toeplitz": toeplitz,
         "forward_projector": forward,
         "nonneg_solve": nonneg,
+        "fcr": fcr,
         "cg_iters_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
         "cg_iters": iters,
         "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},

@@ -19,6 +19,6 @@ Conventions (the paper's Section 3.1):
 """
 from .generate import (  # noqa: F401
     Blobs, phantom_blobs, blob_volume, haar_rotations, vmf_rotations,
-    cap_rotations, mixed_rotations, project_blobs, add_noise, uniform_shifts,
+    cap_rotations, mixed_rotations, rct_rotations, project_blobs, add_noise, uniform_shifts,
     ctf_group_table, config_inputs, CONFIGS, BATCH, batch_inputs,
 )

@@ -124,6 +124,17 @@ def cap_rotations(M: int, cap_deg: float, pole, seed) -> np.ndarray:
     return _frame_from_direction(d, rng.uniform(0, 2 * np.pi, M))
 
 
+def rct_rotations(M: int, tilt_deg: float, seed) -> np.ndarray:
+    """Random conical tilt: every viewing direction at polar angle tilt_deg from the
+    z axis, azimuth uniform on [0, 2 pi), in-plane angle uniform.  The slices then miss
+    the cone of half-angle 90 - tilt_deg about z in Fourier space."""
+    rng = _rng(seed)
+    t = np.deg2rad(tilt_deg)
+    phi = rng.uniform(0, 2 * np.pi, M)
+    d = np.stack([np.sin(t) * np.cos(phi), np.sin(t) * np.sin(phi), np.full(M, np.cos(t))], axis=1)
+    return _frame_from_direction(d, rng.uniform(0, 2 * np.pi, M))
+
+
 def mixed_rotations(M: int, seed, frac_vmf=0.7, kappa=20.0, n_axes=3) -> np.ndarray:
     """frac_vmf of the views vMF(kappa) about n_axes random axes, the rest Haar."""
     rng = _rng(seed)
@@ -205,6 +216,11 @@ CONFIGS = {
     "C5": dict(N=128, M=40000, n_blobs=60, views="cap", shift_px=2.0,
                defocus_um=list(np.linspace(1.0, 3.5, 8)), snr=0.1, lam=1e-3, iters=2000,
                rel_tol=1e-4, seeds=(41, 42, 43)),
+    # random conical tilt series (tilt 60 deg, azimuth uniform), SNR 1, shaped like the
+    # paper's simulation (90^3 volume, 10,000 images; N = 96 is the nearest supported
+    # size); no CTF in the images (the generator holds none), so none in the solve
+    "RCT": dict(N=96, M=10000, n_blobs=40, views="rct", shift_px=2.0, defocus_um=None,
+                snr=1.0, lam=1e-3, iters=2000, rel_tol=1e-4, seeds=(51, 52, 53), tilt_deg=60.0),
 }
 
 
@@ -225,6 +241,8 @@ def config_inputs(name: str, M: int | None = None, N: int | None = None, images:
         R = haar_rotations(M, rng)
     elif cfg["views"] == "mixed":
         R = mixed_rotations(M, rng)
+    elif cfg["views"] == "rct":
+        R = rct_rotations(M, cfg["tilt_deg"], rng)
     elif cfg["views"] == "cap":
         n_cap = int(round(0.85 * M))
         R = np.concatenate([cap_rotations(n_cap, 15.0, [0, 0, 1], rng),
