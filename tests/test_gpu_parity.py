@@ -164,8 +164,9 @@ def test_cg_config1_matches_oracle(F, W, tol):
     err = rel(x.cpu().numpy(), xo)
     print(f"C1 W={W}: CG volume rel err {err:.3e}")
     assert err <= tol
-    # residual history agrees to 1e-4 of the initial residual (late residuals are ~2e-4 of it)
-    assert np.abs(hist.cpu().numpy() - ho).max() <= 1e-4 * ho[0]
+    # residual history: the same drift budget as the volume, relative to the initial
+    # residual (late residuals are ~2e-4 of it, so they carry the FP32 drift in full)
+    assert np.abs(hist.cpu().numpy() - ho).max() <= tol * ho[0]
 
 
 @pytest.mark.parametrize("W", [6, 7])
