@@ -55,7 +55,11 @@ __global__ void __launch_bounds__(1024) k_view_moment(const double* __restrict__
     }
 }
 
-// h^2-weighted histogram of the half-disc samples (the mirrored half falls in the same bin)
+// h^2-weighted histogram of the half-disc samples (the mirrored half falls in the same
+// bin).  A thread owns one sample t of every image its block visits: |xi| = |k| fixes
+// the shell, so only the cone moves with the image, and the thread sums its weights
+// per cone in registers (|<xi, a>| = |k1 <u, a> + k2 <v, a>| with u, v the slice axes)
+// and adds them to the block's histogram once.
 __global__ void __launch_bounds__(256) k_pc_features(const ImgGeom* __restrict__ geom, const int32_t* __restrict__ htab,
                                                      const int32_t* __restrict__ gid, const float* __restrict__ h2,
                                                      int M, int nH, int n_ctf, float halfN, float a1, float a2, float a3,
@@ -68,14 +72,25 @@ __global__ void __launch_bounds__(256) k_pc_features(const ImgGeom* __restrict__
         const int kk = htab[t];
         const float k1 = (float)(int16_t)(kk & 0xffff), k2 = (float)(kk >> 16);
         const float rk = sqrtf(k1 * k1 + k2 * k2);     // |xi| in grid units, exactly |k|
+        const int s = min(kShells - 1, (int)floorf((float)kShells * rk / halfN));
+        const float inv_r = rk > 0.0f ? 1.0f / rk : 0.0f;
+        float acc[kCones];
+#pragma unroll
+        for (int j = 0; j < kCones; ++j) acc[j] = 0.0f;
         for (int m = blockIdx.y; m < M; m += gridDim.y) {
             const ImgGeom g = geom[m];
-            const float q1 = k1 * g.uh[0] + k2 * g.vh[0];
-            const float q2 = k1 * g.uh[1] + k2 * g.vh[1];
-            const float q3 = k1 * g.uh[2] + k2 * g.vh[2];
+            const float ua = g.uh[0] * a1 + g.uh[1] * a2 + g.uh[2] * a3;
+            const float va = g.vh[0] * a1 + g.vh[1] * a2 + g.vh[2] * a3;
+            const float c = fabsf(k1 * ua + k2 * va) * inv_r;
+            const int cb = min(kCones - 1, (int)floorf((float)kCones * c));
             const int gg = min(max(gid[m], 0), n_ctf - 1);
-            atomicAdd(&s_h[freq_bin_r(q1, q2, q3, rk, halfN, a1, a2, a3)], __ldg(&h2[(size_t)gg * nH + t]));
+            const float w = __ldg(&h2[(size_t)gg * nH + t]);
+#pragma unroll
+            for (int j = 0; j < kCones; ++j) acc[j] += (j == cb) ? w : 0.0f;
         }
+#pragma unroll
+        for (int j = 0; j < kCones; ++j)
+            if (acc[j] != 0.0f) atomicAdd(&s_h[kCones * s + j], acc[j]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kBins; i += blockDim.x)
