@@ -419,12 +419,54 @@ __global__ void __launch_bounds__(kThreads) k_image_dft(const ImgArgs a) {
     const int m = blockIdx.x;
     const size_t img0 = (size_t)m * N * N;
     constexpr int ROWS = img_rows<N>();
-    for (int r0 = 0; r0 < N; r0 += ROWS) {
-        const int nl = min(ROWS, N - r0);
-        auto ld = [&](int line, int n) { return make_float2(img_val<N, T>(a.images, img0 + (size_t)(r0 + line) * N + n), 0.0f); };
-        auto st = [&](int line, int k, float2 v) { if (k <= N / 2) S1[(r0 + line) * H1 + k] = v; };
+    // rows 2j and 2j+1 (real) transformed together as z = x_2j + i x_2j+1: Z[k] for
+    // k <= N/2 goes to row 2j's slots, Z[k] for k > N/2 to row 2j+1's (slot k - N/2 - 1)
+    constexpr int NP = N / 2;
+    for (int l0 = 0; l0 < NP; l0 += ROWS) {
+        const int nl = min(ROWS, NP - l0);
+        auto ld = [&](int line, int n) {
+            const size_t i = img0 + (size_t)(2 * (l0 + line)) * N + n;
+            return make_float2(img_val<N, T>(a.images, i), img_val<N, T>(a.images, i + N));
+        };
+        auto st = [&](int line, int k, float2 v) {
+            const int j = l0 + line;
+            if (k < H1) S1[(2 * j) * H1 + k] = v;
+            else S1[(2 * j + 1) * H1 + (k - H1)] = v;
+        };
         block_fft<N, -1, false>(nl, ld, st, scr, a.tw);
     }
+    // the two real rows' half spectra, in place: X_2j[k] = (Z[k] + conj Z[N-k]) / 2,
+    // X_2j+1[k] = (Z[k] - conj Z[N-k]) / 2i.  Task q < N/4 owns k = q and
+    // k' = N/2 - 1 - q, whose four slots hold exactly the Z values both need (Z[N-k] of
+    // one is in the other's row-2j+1 slot); task q = N/4 takes k = N/2.
+    for (int it = threadIdx.x; it < NP * (N / 4 + 1); it += blockDim.x) {
+        const int j = it / (N / 4 + 1), q = it % (N / 4 + 1);
+        float2* A = S1 + (2 * j) * H1;
+        float2* B = S1 + (2 * j + 1) * H1;
+        if (q == N / 4) {                                   // k = N/2: Z[N - k] = Z[k]
+            const float2 z = A[N / 2];
+            A[N / 2] = make_float2(z.x, 0.0f);
+            B[N / 2] = make_float2(z.y, 0.0f);
+            continue;
+        }
+        const int k2 = N / 2 - 1 - q;
+        const float2 zk2 = A[k2], zm2 = B[q];               // Z[k'], Z[N - k']
+        float2 xa1, xb1;
+        if (q == 0) {                                       // k = 0: Z[N - k] = Z[0]
+            const float2 z0 = A[0];
+            xa1 = make_float2(z0.x, 0.0f);
+            xb1 = make_float2(z0.y, 0.0f);
+        } else {
+            const float2 zk = A[q], zm = B[k2];             // Z[k], Z[N - k]
+            xa1 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            xb1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        }
+        A[q] = xa1;
+        B[q] = xb1;
+        A[k2] = make_float2(0.5f * (zk2.x + zm2.x), 0.5f * (zk2.y - zm2.y));
+        B[k2] = make_float2(0.5f * (zk2.y + zm2.y), -0.5f * (zk2.x - zm2.x));
+    }
+    __syncthreads();
     constexpr int CT = img_col_tile<N>();
     for (int c0 = 0; c0 < H1; c0 += CT) {
         const int nl = min(CT, H1 - c0);
