@@ -496,6 +496,16 @@ def main():
     (ms_step,), (ms_per_recon,) = job_time([ms_total / args.steps], world, dev)
     stages = {k: v / args.steps for k, v in stage_acc.items()}
 
+    # the true relative residual of the returned volume, ||A*b - (A*A + lam_eff) x|| / ||A*b||,
+    # recomputed with one Toeplitz apply (the solve stops on the recurrence residual)
+    y_true = torch.empty_like(x)
+    rhs_true = torch.empty_like(x)
+    rec.toeplitz_apply(x, y_true)
+    rec.copy_out(L.FIRM_OUT_RHS, rhs_true)
+    torch.cuda.synchronize(dev)
+    rh = rhs_true.cpu().numpy().astype(np.float64)
+    true_rel_res = float(np.linalg.norm(rh - y_true.cpu().numpy().astype(np.float64)) / np.linalg.norm(rh))
+
     # end-to-end through the C ABI with host (pinned) buffers, copies inside the region
     e2e = None
     if not args.no_e2e:
@@ -674,6 +684,7 @@ def main():
         "fcr": fcr,
         "cg_iters_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
         "cg_iters": iters,
+        "true_rel_residual": true_rel_res,
         "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},
         "roofline": {"kernel": kname, "bound": "alu",
                      "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tatomic/s",
