@@ -3,7 +3,7 @@
 One step = one whole reconstruction of the N=128, 50,000-image workload (FIRM steps
 1-4: image DFTs, spreading into A*b and the Toeplitz kernel, fine-grid transforms,
 circulant K-hat, CG to relative residual 1e-4) with the inputs already resident in
-HBM.  Prints one JSON line (see the design doc for every key).
+HBM.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl firm|reference]
 

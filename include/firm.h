@@ -210,8 +210,8 @@ int firm_solve_nonneg(firm_plan_t plan, float* x, int max_iter, double rel_tol, 
  * mu = 0 (the default) switches it off.  FIRM_EINVAL: mu < 0 or not finite. */
 int firm_set_damping(firm_plan_t plan, double mu);
 
-/* Preconditioner used by firm_cg_solve from its next call on (north star; the paper's
- * CG is unpreconditioned).  FIRM_PRECOND_NONE: plain CG (Section 3.3).
+/* Preconditioner used by firm_cg_solve from its next call on (an addition to the
+ * paper, whose CG is unpreconditioned).  FIRM_PRECOND_NONE: plain CG (Section 3.3).
  * FIRM_PRECOND_CIRCULANT: z = F^-1 diag(1 / (kappa(k) + lam_eff)) F r on the N^3 grid,
  * kappa the spectrum of T. Chan's optimal circulant of the Toeplitz operator (the
  * circulant nearest to it in Frobenius norm; column sum over n = m mod N of
@@ -227,7 +227,7 @@ int firm_set_damping(firm_plan_t plan, double mu);
 enum { FIRM_PRECOND_NONE = 0, FIRM_PRECOND_CIRCULANT = 1, FIRM_PRECOND_BINNED = 2, FIRM_PRECOND_TABLE = 3 };
 int firm_set_precond(firm_plan_t plan, int mode);
 
-/* Learned-preconditioner interface (north star; no counterpart in the paper).  Bins: a
+/* Learned-preconditioner interface (no counterpart in the paper).  Bins: a
  * frequency q (N-grid units) is in shell s = min(63, floor(64 |q| / (N/2))) and cone
  * c = min(15, floor(16 |<q/|q|, a>|)), bin = 16 s + c, a = firm_pc_axis (eigenvector of
  * the largest eigenvalue of the second moment of the viewing directions R_m^T e3 of

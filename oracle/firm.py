@@ -436,8 +436,8 @@ def projected_cg(apply, rhs: np.ndarray, max_iter: int, rel_tol: float = 0.0):
 
 
 # ----------------------------------------------------------------------------
-# Circulant preconditioner (north star; built on the circulant diagonalisation of
-# Section 2.3, eq. circ1)
+# Circulant preconditioner (an addition to the paper; built on the circulant
+# diagonalisation of Section 2.3, eq. circ1)
 # ----------------------------------------------------------------------------
 
 def wrapped_spectrum(Ker: np.ndarray, weighted: bool = True) -> np.ndarray:

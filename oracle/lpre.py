@@ -1,6 +1,6 @@
 """FP64 oracle of the learned Fourier-domain CG preconditioner -- test infrastructure only.
 
-Not in the paper (the benchmark spec adds it; the paper's CG, Section 3.3, is
+Not in the paper (an addition to it; the paper's CG, Section 3.3, is
 unpreconditioned).  Definitions:
 
   * bins: a frequency vector q (in units of the N-grid, |q| <= ~N/2) falls in shell

@@ -859,11 +859,12 @@ cudaError_t launch_toeplitz(Plan& P, const float* x, float* y, const float2* cg_
 }
 
 // ---------------------------------------------------------------------------
-// Preconditioner z = F^-1 diag(d) F r on the N^3 grid (PCG; the benchmark spec).  Five
-// passes like the Toeplitz apply without padding: real rows forward (half
-// spectrum), y forward, z forward x d x z inverse, y inverse, Hermitian rows
-// inverse with <r, z> reduced and beta = <r,z>_new / <r,z>_old set on the device.
-// d already holds the 1/N^3 of the inverse transform.
+// Preconditioner z = F^-1 diag(d) F r on the N^3 grid (PCG; an addition to the
+// paper, whose CG is unpreconditioned).  Three launches, like the Toeplitz apply
+// without padding: per z-plane real rows forward (half spectrum) and y forward; z
+// forward x d x z inverse; per z-plane y inverse and Hermitian rows inverse with
+// <r, z> reduced and the flexible beta set on the device.  d already holds the 1/N^3
+// of the inverse transform.
 // ---------------------------------------------------------------------------
 #define FIRM_SWITCH_N(Nval, ...)                                                              \
     switch (Nval) {                                                                          \

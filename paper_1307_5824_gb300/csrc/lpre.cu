@@ -1,5 +1,5 @@
-// lpre.cu -- the learned Fourier-domain CG preconditioner (north star; the paper's CG,
-// Section 3.3, is unpreconditioned).
+// lpre.cu -- the learned Fourier-domain CG preconditioner (an addition to the paper,
+// whose CG, Section 3.3, is unpreconditioned).
 //
 // Bins: a frequency vector q in N-grid units falls in shell s = min(63, floor(64|q|/(N/2)))
 // and cone c = min(15, floor(16 |<q/|q|, a>|)), a the principal axis of the viewing

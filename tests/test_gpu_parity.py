@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Gates (the benchmark spec): Ker and A*b to relative L2 <= 1e-5, the CG volume to
+Gates: Ker and A*b to relative L2 <= 1e-5, the CG volume to
 relative L2 <= 1e-4 after the same iteration count.  The FP32 path's own budget
 on top of the window error is derived in the design notes; tolerances are
 written in each test.
