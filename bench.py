@@ -660,7 +660,7 @@ def main():
                "first_shell_outside_below_0.5": int(below[0]) + 1 if below.size else None}
 
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and world == 1:                 # the oracle baseline: rank 0 at N=1 only
         est, sample, parts = oracle_sample(inp, iters)
         cpu = {"value": est, "unit": "s/recon", "cores": cores_used(), "kind": "oracle", "sample": sample,
                "parts": parts}
