@@ -225,7 +225,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    inp = workload(args.images)
+    inp = workload(args.images, args.N, args.workload if args.workload != "C4" else "C3")
     iters_guess = 200
     for _ in range(max(0, args.warmup)):
         pass   # the oracle has no warm-up state; samples below are timed independently
@@ -238,9 +238,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/recon", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "N=128 volume, 50000 BF16 128x128 images (60-blob phantom, Haar views, "
-                                  "20 defocus groups, SNR 0.05), lambda=1e-3, CG to rel-res 1e-4",
-                      "N": 128, "M": inp["M"]},
+           "config": {"workload": workload_name(inp, args.W, args.precond, args.workload),
+                      "N": inp["N"], "M": inp["M"], "W": args.W, "precond": args.precond},
            "cpu_baseline": {"value": v, "unit": "s/recon", "cores": cores_used(), "kind": "oracle",
                             "sample": sample + f"; CG iteration count assumed {iters_guess}"},
            "e2e": {"value": v, "unit": "s/recon", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
