@@ -684,6 +684,10 @@ def main():
         "cg_iters_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
         "cg_iters": iters,
         "true_rel_residual": true_rel_res,
+        # the kernel channel (binning and spreading of Ker, its transform, K-hat) depends
+        # on the poses only: a one-time precompute for a fixed pose set
+        "s_per_recon_without_precompute": (ms_per_recon - sum(stages.get(k, 0.0) for k in
+                                                              ("bin_ker", "spread_ker", "fft_ker", "khat"))) / 1e3,
         "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},
         "roofline": {"kernel": kname, "bound": "alu",
                      "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tatomic/s",
