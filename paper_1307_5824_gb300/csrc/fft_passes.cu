@@ -9,11 +9,17 @@
 //   K-hat       eq. embedding_circulant / eq. circ1: the 2N^3 circulant column gathered
 //               from the Ker half box, transformed, real part kept on j1 in [0, N].
 //   A*b         eq. backprojection: 2N^3 complex fine grid -> N^3, 2 Re / phihat.
-//   Toeplitz    eq. property via Section 3.2: x padded to 2N^3, forward along x (real
-//               rows, half spectrum kept), y, then z-forward x K-hat x z-inverse in one
-//               pass, y-inverse and x-inverse (Hermitian rows) with the crop, 1/(2N)^3
-//               and lam_eff x fused; optionally the CG update p = r + beta p in the
-//               first pass and the FP64 partial sums of <p, Ap> in the last.
+//   Toeplitz    eq. property via Section 3.2: x padded to 2N^3; per z-plane, forward
+//               along x (real rows, half spectrum kept) and y with the plane held in
+//               shared memory; z-forward x K-hat x z-inverse in one pass; per z-plane,
+//               y-inverse and x-inverse (Hermitian rows) with the crop, 1/(2N)^3 and
+//               lam_eff x fused; optionally the CG update p = r + beta p in the first
+//               pass and the FP64 partial sums of <p, Ap> in the last.  The first-
+//               difference damping (Section 5) is added to K-hat once (k_khat_damp).
+//   PCG         the Fourier-diagonal preconditioner on N^3 in the same three-launch
+//               form (not in the paper).
+//   A V         the forward projector's transform (type-2 NUFFT): V / phihat with the
+//               centring sign, zero-padded to (2N)^3, forward along x, y, z in place.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

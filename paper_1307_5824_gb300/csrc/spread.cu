@@ -16,6 +16,9 @@
 //              (8 + W)^3 shared-memory region in int32 fixed point (native shared
 //              atomics), folds it into FP32 every 512 or 1024 points, then adds the region
 //              into the FP64 global grid with FP64 atomics.
+// The forward projector's interpolation (k_interp, at the end of this file) is the
+// transpose of step 2 on the same binning: a CTA stages its brick's region of the
+// transformed grid and gathers the W^3 taps of each point, with no atomics.
 #include <cuda_runtime.h>
 
 #include "firm_internal.h"
