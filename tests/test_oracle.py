@@ -715,3 +715,37 @@ def test_projected_cg_is_cg_when_the_solution_is_positive():
     assert ok and np.linalg.norm(x.ravel() - xt) <= 1e-9 * np.linalg.norm(xt)
     xc, _, _ = O.cg(apply, b.reshape(4, 4, 4), its)
     assert np.linalg.norm(x - xc) <= 1e-9 * np.linalg.norm(xc)   # no bound ever hit: the same iterates
+
+
+# -- readings 1 and 2 written out on single entries -----------------------------------
+def test_circulant_index_map_places_each_lag_at_its_wrapped_index():
+    """Reading 2 (eq. embedding_index, read 0-based): a kernel that is 1 at one lag
+    n in (-N, N)^3 and 0 elsewhere puts its 1 at index i_j = n_j mod 2N of the circulant
+    column, and nowhere else; a lag with some n_j = -N (the planes i_j = N) is dropped."""
+    N = 4
+    for lag in [(0, 0, 0), (1, -2, 3), (-3, 3, -1), (-1, 0, 2)]:
+        Ker = np.zeros((2 * N,) * 3)
+        Ker[lag[0] + N, lag[1] + N, lag[2] + N] = 1.0
+        C = O.circulant_column(Ker)
+        assert C.sum() == 1.0
+        assert C[tuple(l % (2 * N) for l in lag)] == 1.0
+    Ker = np.zeros((2 * N,) * 3)
+    Ker[0, N + 1, N] = 1.0                               # lag (-N, 1, 0)
+    assert O.circulant_column(Ker).sum() == 0.0
+    assert O.circulant_column(Ker, "ker")[N, 1, 0] == 1.0   # kept when asked, at i = N
+
+
+def test_image_dft_at_plus_half_n_is_the_periodic_value():
+    """Reading 1: the symmetric disc includes k_j = +N/2, whose value is the DFT's at
+    -N/2 (the centred DFT of integer pixel positions is N-periodic in k); with a shift
+    the phase exp(2 pi i <k, s>/N) differs between the two by exp(2 pi i N s_j / N)."""
+    rng = np.random.default_rng(91)
+    N = 8
+    img = rng.standard_normal((2, N, N))
+    K = np.array([[N // 2, 0], [-N // 2, 0], [0, N // 2], [0, -N // 2], [N // 2, N // 2 - 2]])
+    b = O.image_dft(img, K)
+    assert np.allclose(b[:, 0], b[:, 1]) and np.allclose(b[:, 2], b[:, 3])
+    s = np.array([[0.3, -0.7], [1.25, 0.5]])
+    bs = O.image_dft(img, K, s)
+    assert np.allclose(bs[:, 0], b[:, 0] * np.exp(2j * np.pi * (N // 2) * s[:, 0] / N))
+    assert np.allclose(bs[:, 1], b[:, 1] * np.exp(-2j * np.pi * (N // 2) * s[:, 0] / N))
