@@ -299,11 +299,14 @@ int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y);
  *   lam_eff Tikhonov weight added (>= 0), e.g. firm_lambda_eff of that plan.
  *   x, y    N^3 float32 device arrays, distinct.
  *   stream  cudaStream_t the passes are queued on; the call does not wait.
- * The first call on a device looks up the array's device address (once per device,
- * under a lock); make that first call before any stream capture.  All calls share the
- * one array: calls whose work overlaps on the GPU (other streams, other threads) race
- * and must be serialised by the caller.  Every pass writes its scratch before reading
- * it, so nothing has to start at zero. */
+ * All four pointers must be memory of the current device; anything else is rejected
+ * with FIRM_EINVAL.  The first call on a device does a one-time set-up: it looks up the
+ * array's device address and writes the FFT twiddles of every supported N into it with
+ * a synchronous copy (once per device, under a lock); make that first call before any
+ * stream capture.  Later calls only queue kernels.  All calls share the one array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Every pass writes its scratch before reading it, so
+ * nothing has to start at zero. */
 int firm_toeplitz_apply_static(int N, const float* khat, double lam_eff, const float* x, float* y, void* stream);
 
 /* lam_eff of the last firm_kernel (Tikhonov weight actually added to A*A). */

@@ -1159,11 +1159,19 @@ cudaError_t launch_pc_build_circulant(Plan& P) {
 constexpr int kStaticMaxN = 64;
 constexpr size_t kStaticT1 = (size_t)kStaticMaxN * kStaticMaxN * (kStaticMaxN + 1);       // N x N x (N+1)
 constexpr size_t kStaticT2 = (size_t)kStaticMaxN * 2 * kStaticMaxN * (kStaticMaxN + 1);   // N x 2N x (N+1)
-constexpr size_t kStaticTw = 2 * kStaticMaxN;                                             // 2N twiddles
+// One twiddle slot per transform length L = 2N (32, 64, 96, 128), back to back:
+// slot(L) starts at 32 + 64 + ... + (L - 32), 320 float2 in all.
+constexpr size_t kStaticTw = 32 + 64 + 96 + 128;
 static __device__ __align__(256) float2 g_static_scratch[kStaticT1 + kStaticT2 + kStaticTw];
 
-// Device address of g_static_scratch for the current device, looked up once per
-// device (host code cannot use the symbol itself as a device pointer).
+static constexpr size_t static_tw_slot(int L) {
+    return kStaticT1 + kStaticT2 + (size_t)(L / 32 - 1) * (L / 32) / 2 * 32;
+}
+
+// Device address of g_static_scratch on the current device.  Host code cannot use
+// the symbol itself as a device pointer, so the address is looked up once per
+// device, under a lock, and the twiddle slots are written then, with a synchronous
+// copy: later calls queue kernels only.
 static int static_scratch(float2** out) {
     static std::mutex mu;
     static void* addr[256] = {};
@@ -1174,6 +1182,16 @@ static int static_scratch(float2** out) {
     if (!addr[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return FIRM_ECUDA;
+        float2 tw_h[kStaticTw];           // on the stack: no heap either
+        for (int L = 32; L <= 2 * kStaticMaxN; L += 32) {
+            float2* slot = tw_h + (static_tw_slot(L) - kStaticT1 - kStaticT2);
+            for (int j = 0; j < L; ++j) {
+                const double a = -2.0 * 3.14159265358979323846 * j / L;
+                slot[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+        }
+        float2* tw_d = reinterpret_cast<float2*>(p) + kStaticT1 + kStaticT2;
+        if (cudaMemcpy(tw_d, tw_h, sizeof(tw_h), cudaMemcpyHostToDevice) != cudaSuccess) return FIRM_ECUDA;
         addr[dev] = p;
     }
     *out = reinterpret_cast<float2*>(addr[dev]);
@@ -1185,14 +1203,8 @@ static cudaError_t toeplitz_static_l(float2* scratch, const float* khat, const f
                                      cudaStream_t s) {
     float2* t1 = scratch;
     float2* t2 = scratch + kStaticT1;
-    float2* tw = scratch + kStaticT1 + kStaticT2;
-    float2 tw_h[L];                       // on the stack: no heap either
-    for (int j = 0; j < L; ++j) {
-        const double a = -2.0 * 3.14159265358979323846 * j / L;
-        tw_h[j] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    cudaError_t e = cudaMemcpyAsync(tw, tw_h, sizeof(tw_h), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
+    const float2* tw = scratch + static_tw_slot(L);
+    cudaError_t e;
     constexpr int ROWS = rows_per_block<L>();
     const size_t smem_rows = sizeof(float2) * smem_elems<L, false>(ROWS);
     const size_t smem_cols = sizeof(float2) * smem_elems<L, true>(TX<L>());
@@ -1222,13 +1234,17 @@ static cudaError_t toeplitz_static_l(float2* scratch, const float* khat, const f
 
 }  // namespace firm
 
+// True when p is device (or managed) memory of the current device: the static
+// array used with it is the current device's copy.
 static bool on_device(const void* p) {
     cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 extern "C" int firm_toeplitz_apply_static(int N, const float* khat, double lam_eff, const float* x, float* y,
