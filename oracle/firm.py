@@ -260,6 +260,25 @@ def backproject_at(images, shifts, R, h, K, nvox):
 # Toeplitz structure, circulant embedding, CG
 # ----------------------------------------------------------------------------
 
+def _fftn(a):
+    """Library 3-D FFT (exponent -i): scipy.fft on all host threads when scipy is present
+    (the same transform; only the 1-D batches are split across threads), numpy otherwise."""
+    try:
+        import scipy.fft as sf
+    except ImportError:
+        return np.fft.fftn(a)
+    return sf.fftn(a, workers=-1)
+
+
+def _ifftn(a):
+    """Inverse of _fftn (exponent +i, divided by the number of points)."""
+    try:
+        import scipy.fft as sf
+    except ImportError:
+        return np.fft.ifftn(a)
+    return sf.ifftn(a, workers=-1)
+
+
 def circulant_column(Ker: np.ndarray, lag_n_planes: str = "zero") -> np.ndarray:
     """First column of the 2N^3 circulant C^A (eq. embedding_circulant, reading 2).
 
@@ -278,7 +297,7 @@ def circulant_column(Ker: np.ndarray, lag_n_planes: str = "zero") -> np.ndarray:
 
 def khat(Ker: np.ndarray, lag_n_planes: str = "zero") -> np.ndarray:
     """Eigenvalues of C^A: the 3D FFT of its first column (eq. circ1).  Complex (2N)^3."""
-    return np.fft.fftn(circulant_column(Ker, lag_n_planes))
+    return _fftn(circulant_column(Ker, lag_n_planes))
 
 
 def khat_half(Ker: np.ndarray) -> np.ndarray:
@@ -314,7 +333,7 @@ def toeplitz_apply(Khat: np.ndarray, V: np.ndarray, lam_eff: float = 0.0) -> np.
     N = V.shape[0]
     pad = np.zeros((2 * N,) * 3, complex)
     pad[:N, :N, :N] = V
-    y = np.fft.ifftn(Khat * np.fft.fftn(pad))[:N, :N, :N]
+    y = _ifftn(Khat * _fftn(pad))[:N, :N, :N]
     return y + lam_eff * V
 
 
