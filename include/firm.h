@@ -30,6 +30,9 @@
  * outputs are copied back before the call returns.  Device arrays are read or
  * written in stream order on the plan's stream; the call returns without waiting
  * unless a host output, a host residual history or a relative tolerance needs it.
+ * In particular firm_kernel and firm_backproject with device inputs and outputs (or
+ * null outputs) queue their work and return: lam_eff, Ker(0) and the principal viewing
+ * axis stay on the device until a query (firm_lambda_eff, firm_pc_axis) reads them.
  *
  * Ownership: the caller owns every array it passes, including the plan's
  * workspace (firm_workspace_size / firm_plan); the library allocates no device
@@ -58,7 +61,12 @@ typedef enum {
     FIRM_ENOTCONV = 4,    /* CG reached max_iter above rel_tol */
     FIRM_EBREAKDOWN = 5,  /* CG breakdown: <p, Ap> <= 0 or a non-finite scalar */
     FIRM_ETIMEOUT = 6,    /* a bounded device wait gave up (never expected) */
-    FIRM_ESTATE = 7       /* call order: e.g. firm_cg_solve before firm_kernel */
+    FIRM_ESTATE = 7,      /* call order: e.g. firm_cg_solve before firm_kernel */
+    FIRM_EINTERNAL = 8    /* an internal invariant failed on the device (a binned point
+                           * outside its brick; never expected).  Device kernels record it
+                           * in the plan; it is reported, and cleared, by the next call that
+                           * waits for the stream (a host output, firm_cg_solve,
+                           * firm_lambda_eff, firm_pc_axis), not by the call that queued it. */
 } firm_status;
 
 enum { FIRM_IMG_F32 = 0, FIRM_IMG_BF16 = 1 };
@@ -83,7 +91,7 @@ typedef struct {
     int lambda_mode;  /* FIRM_LAMBDA_RELATIVE: lam_eff = lambda * Ker(0); ABSOLUTE: lambda */
     int disc_mode;    /* 0: symmetric disc |k| <= N/2 (the only mode of the CUDA path) */
     int img_dtype;    /* FIRM_IMG_F32 or FIRM_IMG_BF16 */
-    int flags;        /* 0, or FIRM_FLAG_FP64_CG */
+    int flags;        /* 0, or FIRM_FLAG_FP64_CG and / or FIRM_FLAG_FUSED */
 } firm_params;
 
 /* FIRM_FLAG_FP64_CG: firm_cg_solve runs CG (Section 3.3) with FP64 vectors and an FP64
@@ -96,12 +104,23 @@ typedef struct {
  * (2N)^3 * 24 + N^3 * 32 bytes. */
 enum { FIRM_FLAG_FP64_CG = 1 };
 
+/* FIRM_FLAG_FUSED: the plan can run firm_kernel_backproject, which spreads both
+ * channels of FIRM steps 2-3 (eq. kernel, eq. backprojection) onto the one 4N^3 fine
+ * grid in a single pass over the slice points.  The workspace grows by 2 (4N)^3
+ * doubles (the complex A*b grid beside the real Ker grid: 2.1 GB at N = 128).  May be
+ * combined with FIRM_FLAG_FP64_CG; not accepted by firm_batch_create. */
+enum { FIRM_FLAG_FUSED = 2 };
+
 typedef struct firm_plan_s* firm_plan_t;
 
-/* Bytes of device workspace a plan with these parameters needs. */
+/* Bytes of device workspace a plan with these parameters needs (the layout of
+ * firm_plan: fine grid, FFT intermediates, CG vectors; Section 3.4 steps 1-4). */
 int firm_workspace_size(const firm_params* p, size_t* bytes);
 
-/* Create a plan: validates p, copies the CTF table (n_groups entries; may be NULL
+/* Create a plan for FIRM's precomputation and CG (Section 3.4, steps 1-4; the CTF of
+ * Section 3.1, the window and deconvolution of the type-1 NUFFT of Section 3.4, the
+ * FFTs of the circulant embedding of Section 3.2): validates p, copies the CTF table
+ * (n_groups entries; may be NULL
  * when n_groups == 0), precomputes the Kaiser-Bessel window polynomials, the
  * deconvolution factors and the FFT tables, and carves `workspace` (device memory,
  * at least firm_workspace_size bytes, 256-byte aligned) into its buffers.  stream is
@@ -124,6 +143,21 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
  * The plan keeps A*b; rhs_out (nullable) receives a copy (N^3 float32). */
 int firm_backproject(firm_plan_t plan, int M, const void* images, const double* shifts,
                      const double* R, const int32_t* group, float* rhs_out);
+
+/* FIRM steps 1-3 in one call, the two spreading channels fused (Section 3.4; eq.
+ * measurement, eq. backprojection, eq. kernel, eq. embedding_circulant, eq. circ1).
+ * Both sums run over the same slice points xi_{m,k} with the same window, so the
+ * points are binned once on the 4N^3 grid (poses only: this runs while a staged image
+ * upload, firm_stage_images, is still landing), the images are transformed to h b on
+ * the disc, and one spreading pass adds h^2 phi to the Ker grid and h b phi to the A*b
+ * grid (complex, 4N^3); Ker (on [-N, N)^3), K-hat, lam_eff and A*b (on N^3, from the
+ * 4N grid: oversampling 4 for its N modes) follow as in firm_kernel and
+ * firm_backproject, whose results it replaces.  Arguments as those two calls;
+ * khat_out and rhs_out are nullable.  FIRM_EINVAL unless the plan was made with
+ * FIRM_FLAG_FUSED.  Host images not staged ahead are copied into the workspace and
+ * transformed before the binning (no overlap). */
+int firm_kernel_backproject(firm_plan_t plan, int M, const void* images, const double* shifts,
+                            const double* R, const int32_t* group, float* khat_out, float* rhs_out);
 
 /* Forward projector A (Section 3.1, eq. forward-projector; with eq. truncation's disc):
  *     (A V)_m(k) = h_m(|w_k|) sum_n V_n exp(-i <n, xi_{m,k}>),  xi = R_m^T (2 pi k / N, 0),
@@ -241,6 +275,13 @@ int firm_set_precond(firm_plan_t plan, int mode);
  * firm_set_precond_table: use d(q) = exp(table_log[bin(q)]) / Ker(0) as the
  *   preconditioner (selects FIRM_PRECOND_TABLE). */
 int firm_pc_features(firm_plan_t plan, float* out1024);
+
+/* The learned network's input for the plan's last kernel, on the device: the features
+ * of firm_pc_features (the h^2-weighted share of the slice samples in each of the 1024
+ * shell x cone bins) mapped to x_b = log(1024 f_b + 1e-3).  out: 1024 float32, host
+ * or device.  Not in the paper (the learned preconditioner is an addition to its CG,
+ * Section 3.3).  FIRM_ESTATE before firm_kernel. */
+int firm_pc_net_input(firm_plan_t plan, float* out);
 int firm_pc_target(firm_plan_t plan, float* out1024);
 int firm_pc_axis(firm_plan_t plan, float* out3);
 /* Fraction of the N^3 frequency grid (FFT index order, q in [-N/2, N/2)) falling in each

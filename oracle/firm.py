@@ -260,14 +260,18 @@ def backproject_at(images, shifts, R, h, K, nvox):
 # Toeplitz structure, circulant embedding, CG
 # ----------------------------------------------------------------------------
 
+FFT_WORKERS = -1     # host threads of the oracle's FFTs (-1: all); 1 for single-core timings
+
+
 def _fftn(a):
-    """Library 3-D FFT (exponent -i): scipy.fft on all host threads when scipy is present
-    (the same transform; only the 1-D batches are split across threads), numpy otherwise."""
+    """Library 3-D FFT (exponent -i): scipy.fft on FFT_WORKERS host threads when scipy is
+    present (the same transform; only the 1-D batches are split across threads), numpy
+    otherwise."""
     try:
         import scipy.fft as sf
     except ImportError:
         return np.fft.fftn(a)
-    return sf.fftn(a, workers=-1)
+    return sf.fftn(a, workers=FFT_WORKERS)
 
 
 def _ifftn(a):
@@ -276,7 +280,7 @@ def _ifftn(a):
         import scipy.fft as sf
     except ImportError:
         return np.fft.ifftn(a)
-    return sf.ifftn(a, workers=-1)
+    return sf.ifftn(a, workers=FFT_WORKERS)
 
 
 def circulant_column(Ker: np.ndarray, lag_n_planes: str = "zero") -> np.ndarray:

@@ -115,13 +115,16 @@ def window_ft(nu, W: int, window: str, beta: float, quadrature: bool | None = No
 
 
 def type1_gridded(R, K, N, weights, L, *, W=12, window="es", sigma=2, beta=None, threads=None,
-                  chunk=1024, spread_only=False):
+                  chunk=1024, spread_only=False, timing=None):
     """f(n) = sum_{m,k} weights(m, k) exp(+i <n, xi_{m,k}>) for n in [-L/2, L/2)^3, stored
     [n3][n2][n1] (complex), by steps 1-3 of the module docstring.
 
     R is (M, 3, 3); K the disc (|K|, 2); weights a callable weights(a, b) returning the
     (b - a, |K|) weights of images a..b-1 (real or complex), so that no (M, |K|) array
-    has to exist at once."""
+    has to exist at once.  timing (a dict, optional) receives the seconds of step 1
+    (with the weights) and of steps 2-3."""
+    import time
+    t_start = time.perf_counter()
     lib = _load()
     threads = threads or default_threads()
     beta = (es_beta(W) if window == "es" else kb_beta(W, sigma)) if beta is None else beta
@@ -145,6 +148,9 @@ def type1_gridded(R, K, N, weights, L, *, W=12, window="es", sigma=2, beta=None,
             raise ValueError("oracle_spread_slices refused its arguments")
     if tau is None:
         tau = np.zeros((G, G, G))
+    t_spread = time.perf_counter()
+    if timing is not None:
+        timing["spread_s"] = t_spread - t_start
     if spread_only:
         return tau
     import scipy.fft
@@ -154,7 +160,10 @@ def type1_gridded(R, K, N, weights, L, *, W=12, window="es", sigma=2, beta=None,
     sel = n % G
     F = F[np.ix_(sel, sel, sel)]
     d = window_ft(n / G, W, window, beta)
-    return F / (d[:, None, None] * d[None, :, None] * d[None, None, :])
+    out = F / (d[:, None, None] * d[None, :, None] * d[None, None, :])
+    if timing is not None:
+        timing["transform_s"] = time.perf_counter() - t_spread
+    return out
 
 
 def _group_h(N, K, groups, group_id):

@@ -14,19 +14,21 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfirm.so")
 
-FIRM_OK, FIRM_EINVAL, FIRM_ENOMEM, FIRM_ECUDA, FIRM_ENOTCONV, FIRM_EBREAKDOWN, FIRM_ETIMEOUT, FIRM_ESTATE = range(8)
+(FIRM_OK, FIRM_EINVAL, FIRM_ENOMEM, FIRM_ECUDA, FIRM_ENOTCONV, FIRM_EBREAKDOWN, FIRM_ETIMEOUT, FIRM_ESTATE,
+ FIRM_EINTERNAL) = range(9)
 FIRM_IMG_F32, FIRM_IMG_BF16 = 0, 1
 FIRM_LAMBDA_RELATIVE, FIRM_LAMBDA_ABSOLUTE = 0, 1
 FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES, FIRM_OUT_BIN_IDS, FIRM_OUT_BIN_WORK = 0, 1, 2, 3, 4, 5
 FIRM_PRECOND_NONE, FIRM_PRECOND_CIRCULANT, FIRM_PRECOND_BINNED, FIRM_PRECOND_TABLE = 0, 1, 2, 3
 FIRM_BATCH_GRAPH, FIRM_BATCH_PERSISTENT = 1, 2
-FIRM_FLAG_FP64_CG = 1
+FIRM_FLAG_FP64_CG, FIRM_FLAG_FUSED = 1, 2
 
 EXPORTED = [
-    "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_stage_images", "firm_cg_solve",
+    "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_kernel_backproject",
+    "firm_stage_images", "firm_cg_solve",
     "firm_forward", "firm_data_residual", "firm_set_damping", "firm_solve_nonneg",
     "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_set_precond", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
-    "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_target", "firm_pc_axis",
+    "firm_stage_times", "firm_launch_count", "firm_pc_features", "firm_pc_net_input", "firm_pc_target", "firm_pc_axis",
     "firm_set_precond_table", "firm_pc_bin_volumes", "firm_pc_baseline", "firm_pc_residual_target", "firm_set_precond_residual",
     "firm_mlp_forward", "firm_mlp_to_bf16", "firm_mlp_forward_bf16", "firm_mlp_grad",
     "firm_mlp_adam", "firm_mlp_param_count", "firm_mlp_work_floats",
@@ -77,6 +79,7 @@ def lib() -> ctypes.CDLL:
                             vp, ctypes.c_size_t, vp]
     L.firm_kernel.argtypes = [vp, i, vp, vp, vp]
     L.firm_backproject.argtypes = [vp, i, vp, vp, vp, vp, vp]
+    L.firm_kernel_backproject.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
     L.firm_stage_images.argtypes = [vp, i, vp, vp, ctypes.c_size_t]
     L.firm_forward.argtypes = [vp, i, vp, vp, vp, vp]
     L.firm_set_damping.argtypes = [vp, d]
@@ -91,7 +94,7 @@ def lib() -> ctypes.CDLL:
     L.firm_set_timing.argtypes = [vp, i]
     L.firm_stage_times.argtypes = [vp, ctypes.POINTER(d), i]
     L.firm_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
-    for n in ("firm_pc_features", "firm_pc_target", "firm_pc_axis", "firm_set_precond_table", "firm_pc_bin_volumes", "firm_pc_baseline",
+    for n in ("firm_pc_features", "firm_pc_net_input", "firm_pc_target", "firm_pc_axis", "firm_set_precond_table", "firm_pc_bin_volumes", "firm_pc_baseline",
               "firm_pc_residual_target", "firm_set_precond_residual"):
         getattr(L, n).argtypes = [vp, vp]
     L.firm_mlp_forward.argtypes = [vp, i, vp, vp, vp, vp]
@@ -190,6 +193,11 @@ def firm_backproject(plan, M: int, images, shifts, R, group=None, rhs_out=None):
            "firm_backproject")
 
 
+def firm_kernel_backproject(plan, M: int, images, shifts, R, group=None, khat_out=None, rhs_out=None):
+    _check(lib().firm_kernel_backproject(plan, M, _ptr(images), _ptr(shifts), _ptr(R), _ptr(group), _ptr(khat_out),
+                                         _ptr(rhs_out)), "firm_kernel_backproject")
+
+
 def firm_stage_images(plan, M: int, images, staging, staging_bytes: int):
     _check(lib().firm_stage_images(plan, M, _ptr(images), _ptr(staging), int(staging_bytes)), "firm_stage_images")
 
@@ -282,6 +290,10 @@ def firm_launch_count(plan) -> int:
 
 def firm_pc_features(plan, out):
     _check(lib().firm_pc_features(plan, _ptr(out)), "firm_pc_features")
+
+
+def firm_pc_net_input(plan, out):
+    _check(lib().firm_pc_net_input(plan, _ptr(out)), "firm_pc_net_input")
 
 
 def firm_pc_target(plan, out):

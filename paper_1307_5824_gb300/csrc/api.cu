@@ -165,13 +165,18 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.tw_4n = c.take<float2>(4 * N);
     w.dec_k = c.take<float>(2 * N);
     w.dec_r = c.take<float>(N);
+    w.dec_r4 = c.take<float>(N);
     w.samples = c.take<float2>(M * nH);
     w.count = c.take<uint32_t>(nb3);
     w.cursor = c.take<uint32_t>(nb3);
     w.work = c.take<int4>(max_work);
     w.item_part = c.take<double>(2 * max_work);
     w.counters = c.take<int>(8);
-    const size_t grid_bytes = std::max(Gk * Gk * Gk * sizeof(double), Gr * Gr * Gr * 2 * sizeof(double));
+    // FP64 fine grid: Ker (4N^3 real) or A*b (2N^3 complex); the fused form holds both
+    // channels on the 4N grid (real Ker, then complex A*b)
+    const bool fused = (p.flags & FIRM_FLAG_FUSED) != 0;
+    const size_t grid_bytes = std::max(Gk * Gk * Gk * sizeof(double) * (fused ? 3 : 1),
+                                       Gr * Gr * Gr * 2 * sizeof(double));
     w.grid = c.take<double>(grid_bytes / sizeof(double));
     // union: staged images | point ids | FFT intermediates (never live together)
     const size_t fx1 = std::max({Gk * Gk * (N + 1), Gr * Gr * N, H3});
@@ -210,6 +215,7 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.hist = c.take<double>(kMaxHist);
     w.cg = c.take<CgState>(1);
     w.lam = c.take<float>(2);
+    w.axis = c.take<float>(4);
     const bool fp64 = (p.flags & FIRM_FLAG_FP64_CG) != 0;
     const size_t L3 = fp64 ? 8 * N3 : 0, n64 = fp64 ? N3 : 0;
     w.tw64 = c.take<double2>(fp64 ? N : 0);
@@ -233,7 +239,7 @@ static int check_params(const firm_params* p) {
     if (p->M < 0 || p->n_groups < 0) return FIRM_EINVAL;
     if (p->W < 6 || p->W > 8) return FIRM_EINVAL;
     if (p->sigma != 2.0) return FIRM_EINVAL;
-    if (p->disc_mode != 0 || (p->flags & ~FIRM_FLAG_FP64_CG) != 0) return FIRM_EINVAL;
+    if (p->disc_mode != 0 || (p->flags & ~(FIRM_FLAG_FP64_CG | FIRM_FLAG_FUSED)) != 0) return FIRM_EINVAL;
     if ((p->flags & FIRM_FLAG_FP64_CG) && p->N != 16 && p->N != 32 && p->N != 64) return FIRM_EINVAL;
     if (p->img_dtype != FIRM_IMG_F32 && p->img_dtype != FIRM_IMG_BF16) return FIRM_EINVAL;
     if (p->lambda_mode != FIRM_LAMBDA_RELATIVE && p->lambda_mode != FIRM_LAMBDA_ABSOLUTE) return FIRM_EINVAL;
@@ -301,11 +307,37 @@ struct StageTimer {
         if ((x) != cudaSuccess) { return FIRM_ECUDA; } \
     } while (0)
 
-static int check_spread_flag(Plan& P) {
+// The spreading and interpolation kernels set counters[2] when a binned point falls
+// outside its brick (an internal invariant; never expected).  Entry points do not wait
+// for it: it is read, and cleared, where the host waits for the stream anyway (a host
+// output, the end of a CG solve, a query of device scalars).
+static int take_device_flag(Plan& P) {
     int flag = 0;
     FIRM_CK(cudaMemcpyAsync(&flag, P.ws.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
     FIRM_CK(cudaStreamSynchronize(P.stream));
-    return flag ? FIRM_ECUDA : FIRM_OK;
+    if (!flag) return FIRM_OK;
+    FIRM_CK(cudaMemsetAsync(P.ws.counters + 2, 0, sizeof(int), P.stream));
+    return FIRM_EINTERNAL;
+}
+
+// An output to dst: device memory is written in stream order; host memory waits for
+// the copy (and reports the device flag).
+static int put_out_checked(Plan& P, void* dst, const void* src, size_t bytes) {
+    if (!dst) return FIRM_OK;
+    if (is_device(dst)) return put_out(dst, src, bytes, P.stream);
+    const int st = put_out(dst, src, bytes, P.stream);
+    return st != FIRM_OK ? st : take_device_flag(P);
+}
+
+// lam_eff and Ker(0) of the last firm_kernel, read from the device (waits for the stream).
+static int read_lam(Plan& P, double* lam_eff, double* ker0) {
+    float lam[2] = {0.f, 0.f};
+    FIRM_CK(cudaMemcpyAsync(lam, P.ws.lam, sizeof(lam), cudaMemcpyDeviceToHost, P.stream));
+    const int st = take_device_flag(P);
+    if (st != FIRM_OK) return st;
+    if (ker0) *ker0 = lam[1] > 0.0f ? lam[1] : 1.0;
+    if (lam_eff) *lam_eff = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda * (double)lam[1] : P.p.lambda;
+    return FIRM_OK;
 }
 
 
@@ -337,8 +369,10 @@ static int compute_target(Plan& P, float* t_host) {
     std::vector<double> s1(1024), s2(1024);
     FIRM_CK(cudaMemcpyAsync(s1.data(), P.ws.pc_s1, 1024 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
     FIRM_CK(cudaMemcpyAsync(s2.data(), P.ws.pc_s2, 1024 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
-    FIRM_CK(cudaStreamSynchronize(P.stream));
-    finalize_target(s1.data(), s2.data(), P.ker0, t_host);
+    double ker0 = 1.0;
+    const int st = read_lam(P, nullptr, &ker0);
+    if (st != FIRM_OK) return st;
+    finalize_target(s1.data(), s2.data(), ker0, t_host);
     return FIRM_OK;
 }
 
@@ -391,7 +425,8 @@ static int cg_solve_fp64(Plan& P, const float* rd, float* x, int max_iter, doubl
     if (iters_out) *iters_out = s.it;
     int st = put_out(x, w.x, n * sizeof(float), P.stream);
     if (st != FIRM_OK) return st;
-    FIRM_CK(cudaStreamSynchronize(P.stream));
+    st = take_device_flag(P);
+    if (st != FIRM_OK) return st;
     if (s.status != FIRM_OK) return s.status;
     if (rel_tol > 0.0 && !(s.rr >= 0.0 && std::sqrt(s.rr) <= s.tol)) return FIRM_ENOTCONV;
     return FIRM_OK;
@@ -478,7 +513,7 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
         return v;
     };
     // deconvolution: (-1)^n / phihat(n / G) for the centred fine grid
-    std::vector<float> dk(2 * N), dr(N);
+    std::vector<float> dk(2 * N), dr(N), dr4(N);
     for (int i = 0; i < 2 * N; ++i) {
         const int n = i - N;
         dk[i] = (float)(((n & 1) ? -1.0 : 1.0) / kb_phihat((double)n / P.Gk, p->W, beta));
@@ -486,6 +521,7 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
     for (int i = 0; i < N; ++i) {
         const int n = i - N / 2;
         dr[i] = (float)(((n & 1) ? -1.0 : 1.0) / kb_phihat((double)n / P.Gr, p->W, beta));
+        dr4[i] = (float)(((n & 1) ? -1.0 : 1.0) / kb_phihat((double)n / P.Gk, p->W, beta));
     }
     const std::vector<float2> t1 = tw(N), t2 = tw(2 * N), t4 = tw(4 * N);
     Workspace& w = P.ws;
@@ -515,6 +551,7 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
     cp(w.tw_4n, t4.data(), sizeof(float2) * 4 * N);
     cp(w.dec_k, dk.data(), sizeof(float) * dk.size());
     cp(w.dec_r, dr.data(), sizeof(float) * dr.size());
+    cp(w.dec_r4, dr4.data(), sizeof(float) * dr4.size());
     std::vector<double2> t64;
     if (p->flags & FIRM_FLAG_FP64_CG) {
         for (int j = 0; j < N; ++j) {
@@ -523,6 +560,8 @@ int firm_plan(firm_plan_t* out, const firm_params* p, const firm_ctf_group* grou
         }
         cp(w.tw64, t64.data(), sizeof(double2) * t64.size());
     }
+    const float axis0[4] = {0.f, 0.f, 1.f, 0.f};
+    cp(w.axis, axis0, sizeof(axis0));
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), P.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
     if (e != cudaSuccess) {
@@ -562,7 +601,6 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     else { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
     FIRM_CK(e);
     FIRM_CK(start_stage(P));                   // a staged image upload runs beside the kernel channel
-    FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
     P.bin_M = -1;
     tm.start(0);
     FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
@@ -581,18 +619,11 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     if (P.p.flags & FIRM_FLAG_FP64_CG) FIRM_CK(launch_khat64(P));
     FIRM_CK(launch_damping(P));
     tm.stop();
-    // lam_eff from Ker(0) (the n = 0 entry of the half box), also kept on the host
-    float ker0 = 0.f;
-    FIRM_CK(cudaMemcpyAsync(&ker0, w.lam + 1, sizeof(float), cudaMemcpyDeviceToHost, P.stream));
-    int st = check_spread_flag(P);
-    if (st != FIRM_OK) return st;
-    P.lam_eff = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda * (double)ker0 : P.p.lambda;
-    P.ker0 = ker0 > 0.0f ? ker0 : 1.0f;
     P.last_M = M;
     if (M > 0) FIRM_CK(launch_view_axis(P, P.cur_R, M));
     P.have_kernel = true;
     P.pc_ready = false;
-    return put_out(khat_out, w.khat, sizeof(float) * 2 * P.N * 2 * P.N * (P.N + 1), P.stream);
+    return put_out_checked(P, khat_out, w.khat, sizeof(float) * 2 * P.N * 2 * P.N * (P.N + 1));
 }
 
 int firm_backproject(firm_plan_t plan, int M, const void* images, const double* shifts, const double* R,
@@ -623,7 +654,6 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
     } else {
         P.cur_images = images;
     }
-    FIRM_CK(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream));
     P.bin_M = -1;
     tm.start(4);
     FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
@@ -640,10 +670,81 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
     tm.start(7);
     FIRM_CK(launch_rhs_transform(P));
     tm.stop();
-    int st = check_spread_flag(P);
-    if (st != FIRM_OK) return st;
     P.have_rhs = true;
-    return put_out(rhs_out, w.rhs, sizeof(float) * P.N * P.N * P.N, P.stream);
+    return put_out_checked(P, rhs_out, w.rhs, sizeof(float) * P.N * P.N * P.N);
+}
+
+int firm_kernel_backproject(firm_plan_t plan, int M, const void* images, const double* shifts, const double* R,
+                            const int32_t* group, float* khat_out, float* rhs_out) {
+    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !images))) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!(P.p.flags & FIRM_FLAG_FUSED)) return FIRM_EINVAL;
+    Workspace& w = P.ws;
+    cudaError_t e = cudaSuccess;
+    StageTimer tm(P);
+    const size_t esz = P.p.img_dtype == FIRM_IMG_BF16 ? 2 : 4;
+    P.cur_R = stage(R, w.R, (size_t)M * 9, P.stream, e);
+    if (group) P.cur_gid = stage(group, w.gid, (size_t)M, P.stream, e);
+    else { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
+    if (shifts) P.cur_shifts = stage(shifts, w.shifts, (size_t)M * 2, P.stream, e);
+    else { if (e == cudaSuccess) e = cudaMemsetAsync(w.shifts, 0, sizeof(double) * 2 * (M > 0 ? M : 1), P.stream); P.cur_shifts = w.shifts; }
+    FIRM_CK(e);
+    const bool staged = M > 0 && P.staged_host == images && P.staged_M == M;
+    // host images not staged ahead are copied into the workspace region the point ids
+    // use, so they are transformed before the binning; otherwise the binning (poses
+    // only) goes first, beside a staged upload
+    const bool host_copy = M > 0 && !staged && !is_device(images);
+    if (staged) FIRM_CK(start_stage(P));
+    P.bin_M = -1;
+    FIRM_CK(launch_geom(P.cur_R, M, w.geom, P.stream));
+    P.launches += M > 0 ? 1 : 0;
+    if (!host_copy) {
+        tm.start(0);
+        FIRM_CK(launch_bin(P, M, true));
+        tm.stop();
+    }
+    if (staged) {
+        FIRM_CK(cudaStreamWaitEvent(P.stream, P.ev_staged, 0));     // the upload has landed
+        P.cur_images = P.staged_dev;
+        P.staged_host = nullptr;
+        P.staged_M = -1;
+    } else if (host_copy) {
+        FIRM_CK(cudaMemcpyAsync(w.images, images, (size_t)M * P.N * P.N * esz, cudaMemcpyHostToDevice, P.stream));
+        P.cur_images = w.images;
+    } else {
+        P.cur_images = images;
+    }
+    tm.start(4);
+    FIRM_CK(launch_image_dft(P, M, P.cur_images, P.cur_shifts, P.cur_gid));
+    if (staged) FIRM_CK(cudaEventRecord(P.ev_stage_read, P.stream));   // staging free again
+    tm.stop();
+    if (host_copy) {
+        tm.start(0);
+        FIRM_CK(launch_bin(P, M, true));
+        tm.stop();
+    }
+    tm.start(1);
+    FIRM_CK(launch_spread_fused(P, M));
+    tm.stop();
+    tm.start(2);
+    FIRM_CK(launch_ker_transform(P));
+    tm.stop();
+    tm.start(3);
+    FIRM_CK(launch_khat(P));
+    FIRM_CK(launch_lam_eff(P));
+    if (P.p.flags & FIRM_FLAG_FP64_CG) FIRM_CK(launch_khat64(P));
+    FIRM_CK(launch_damping(P));
+    tm.stop();
+    tm.start(7);
+    FIRM_CK(launch_rhs_transform4(P));
+    tm.stop();
+    P.last_M = M;
+    if (M > 0) FIRM_CK(launch_view_axis(P, P.cur_R, M));
+    P.have_kernel = P.have_rhs = true;
+    P.pc_ready = false;
+    const int st = put_out_checked(P, khat_out, w.khat, sizeof(float) * 2 * P.N * 2 * P.N * (P.N + 1));
+    if (st != FIRM_OK) return st;
+    return put_out_checked(P, rhs_out, w.rhs, sizeof(float) * P.N * P.N * P.N);
 }
 
 int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging, size_t staging_bytes) {
@@ -675,7 +776,6 @@ static cudaError_t stage_forward_inputs(Plan& P, int M, const float* V, const do
     if (group) P.cur_gid = stage(group, w.gid, (size_t)M, P.stream, e);
     else if (e == cudaSuccess) { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
     Vd = stage(V, w.q, (size_t)P.N * P.N * P.N, P.stream, e);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.counters + 2, 0, sizeof(int), P.stream);
     P.bin_M = -1;
     return e;
 }
@@ -695,9 +795,7 @@ int firm_forward(firm_plan_t plan, int M, const float* V, const double* R, const
     const bool odev = is_device(out);
     float2* od = odev ? reinterpret_cast<float2*>(out) : w.samples;
     FIRM_CK(launch_interp(P, M, ghat, od, nullptr, nullptr));
-    const int st = check_spread_flag(P);
-    if (st != FIRM_OK) return st;
-    if (!odev) return put_out(out, od, sizeof(float2) * (size_t)M * P.nH, P.stream);
+    if (!odev) return put_out_checked(P, out, od, sizeof(float2) * (size_t)M * P.nH);
     return FIRM_OK;
 }
 
@@ -731,9 +829,7 @@ int firm_data_residual(firm_plan_t plan, int M, const float* V, const void* imag
     float2* ghat = reinterpret_cast<float2*>(w.grid);
     FIRM_CK(launch_fwd_transform(P, Vd, ghat));
     FIRM_CK(launch_interp(P, M, ghat, nullptr, w.item_part, w.red_a));
-    const int st = check_spread_flag(P);
-    if (st != FIRM_OK) return st;
-    return put_out(out2, w.red_a, 2 * sizeof(double), P.stream);
+    return put_out_checked(P, out2, w.red_a, 2 * sizeof(double));
 }
 
 int firm_solve_nonneg(firm_plan_t plan, float* x, int max_iter, double rel_tol, int* iters_out) {
@@ -821,7 +917,8 @@ int firm_cg_solve(firm_plan_t plan, const float* rhs, float* x, int max_iter, do
     if (iters_out) *iters_out = s.it;
     int st = put_out(x, w.x, n * sizeof(float), P.stream);
     if (st != FIRM_OK) return st;
-    FIRM_CK(cudaStreamSynchronize(P.stream));
+    st = take_device_flag(P);
+    if (st != FIRM_OK) return st;
     if (s.status != FIRM_OK) return s.status;
     if (rel_tol > 0.0 && !(s.rr >= 0.0 && std::sqrt(s.rr) <= s.tol)) return FIRM_ENOTCONV;
     return FIRM_OK;
@@ -854,14 +951,18 @@ int firm_pc_features(firm_plan_t plan, float* out) {
     Plan& P = plan->P;
     if (!P.have_kernel) return FIRM_ESTATE;
     FIRM_CK(launch_pc_features(P, P.last_M, P.ws.pc_feat));
-    std::vector<float> h(1024);
-    FIRM_CK(cudaMemcpyAsync(h.data(), P.ws.pc_feat, 1024 * sizeof(float), cudaMemcpyDeviceToHost, P.stream));
-    FIRM_CK(cudaStreamSynchronize(P.stream));
-    double tot = 0.0;
-    for (float v : h) tot += v;
-    for (float& v : h) v = tot > 0.0 ? (float)(v / tot) : 0.0f;
-    FIRM_CK(cudaMemcpyAsync(P.ws.pc_feat, h.data(), 1024 * sizeof(float), cudaMemcpyHostToDevice, P.stream));
-    return put_out(out, P.ws.pc_feat, 1024 * sizeof(float), P.stream);
+    FIRM_CK(launch_pc_normalize(P, P.ws.pc_feat, nullptr));
+    return put_out_checked(P, out, P.ws.pc_feat, 1024 * sizeof(float));
+}
+
+int firm_pc_net_input(firm_plan_t plan, float* out) {
+    if (!plan || !out) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    if (!P.have_kernel) return FIRM_ESTATE;
+    float* x = reinterpret_cast<float*>(P.ws.pc_s2);       // 1024 floats of scratch
+    FIRM_CK(launch_pc_features(P, P.last_M, P.ws.pc_feat));
+    FIRM_CK(launch_pc_normalize(P, P.ws.pc_feat, x));
+    return put_out_checked(P, out, x, 1024 * sizeof(float));
 }
 
 int firm_pc_target(firm_plan_t plan, float* out) {
@@ -888,7 +989,10 @@ int firm_pc_baseline(firm_plan_t plan, float* out) {
     if (st != FIRM_OK) return st;
     st = firm_pc_bin_volumes(plan, v.data());
     if (st != FIRM_OK) return st;
-    const double rl = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda : P.p.lambda / (double)P.ker0;
+    double ker0 = 1.0;
+    st = read_lam(P, nullptr, &ker0);
+    if (st != FIRM_OK) return st;
+    const double rl = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda : P.p.lambda / ker0;
     for (int b = 0; b < 1024; ++b)
         t[b] = (float)-std::log((v[b] > 0.0f ? (double)f[b] / (double)v[b] : 0.0) + (rl > 0.0 ? rl : 1e-6));
     if (is_device(out)) {
@@ -962,16 +1066,20 @@ int firm_pc_bin_volumes(firm_plan_t plan, float* out) {
 
 int firm_pc_axis(firm_plan_t plan, float* out3) {
     if (!plan || !out3) return FIRM_EINVAL;
-    if (!plan->P.have_kernel) return FIRM_ESTATE;
-    for (int i = 0; i < 3; ++i) out3[i] = plan->P.pc_axis[i];
+    Plan& P = plan->P;
+    if (!P.have_kernel) return FIRM_ESTATE;
+    float a[4];
+    FIRM_CK(cudaMemcpyAsync(a, P.ws.axis, sizeof(a), cudaMemcpyDeviceToHost, P.stream));
+    const int st = take_device_flag(P);
+    if (st != FIRM_OK) return st;
+    for (int i = 0; i < 3; ++i) out3[i] = a[i];
     return FIRM_OK;
 }
 
 int firm_lambda_eff(firm_plan_t plan, double* out) {
     if (!plan || !out) return FIRM_EINVAL;
     if (!plan->P.have_kernel) return FIRM_ESTATE;
-    *out = plan->P.lam_eff;
-    return FIRM_OK;
+    return read_lam(plan->P, out, nullptr);
 }
 
 int firm_copy_out(firm_plan_t plan, int which, void* dst) {
@@ -1083,6 +1191,7 @@ const char* firm_strerror(int code) {
         case FIRM_EBREAKDOWN: return "CG breakdown";
         case FIRM_ETIMEOUT: return "device wait timed out";
         case FIRM_ESTATE: return "call order (kernel or right-hand side missing)";
+        case FIRM_EINTERNAL: return "internal invariant failed on the device (a binned point outside its brick)";
         default: return "unknown status";
     }
 }

@@ -374,14 +374,11 @@ int firm_batch_wait(firm_batch_t b, int* status, int* iters) {
         Plan& P = b->plans[i]->P;
         CgState s;
         int flag = 0;
-        float lam[2] = {0.f, 0.f};
         if (cudaMemcpy(&s, P.ws.cg, sizeof(CgState), cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(&flag, P.ws.counters + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(lam, P.ws.lam, sizeof(lam), cudaMemcpyDeviceToHost) != cudaSuccess)
+            cudaMemcpy(&flag, P.ws.counters + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
             return FIRM_ECUDA;
-        int sti = flag ? FIRM_ECUDA : s.status;
-        P.lam_eff = P.p.lambda_mode == FIRM_LAMBDA_RELATIVE ? P.p.lambda * (double)lam[1] : P.p.lambda;
-        P.ker0 = lam[1] > 0.0f ? lam[1] : 1.0f;
+        if (flag && cudaMemset(P.ws.counters + 2, 0, sizeof(int)) != cudaSuccess) return FIRM_ECUDA;
+        int sti = flag ? FIRM_EINTERNAL : s.status;
         P.have_kernel = P.have_rhs = true;
         P.pc_ready = false;
         P.cg_iters = s.it;

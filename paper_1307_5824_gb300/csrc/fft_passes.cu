@@ -331,6 +331,26 @@ cudaError_t launch_rhs_transform(Plan& P) {
     return e;
 }
 
+// A*b of the fused form: the complex A*b grid on the 4N fine grid (right after the real
+// Ker grid), transformed along x, y, z with output pruning to the N modes and the
+// deconvolution for oversampling 4 fused into the last pass.
+cudaError_t launch_rhs_transform4(Plan& P) {
+    Workspace& w = P.ws;
+    const int N = P.N, G = P.Gk;
+    const double* grid = w.grid + (size_t)G * G * G;
+    cudaError_t e = cudaSuccess;
+    RhsRowsOp a{{}, grid, w.fx1, w.tw_4n, G * G, G, N};
+    RhsColsYOp b{w.fx1, w.fx2, w.tw_4n, G, N, G, N};
+    RhsColsZOp c{w.fx2, w.rhs, w.dec_r4, w.tw_4n, 1, N * N, G, N};
+    FIRM_SWITCH_4N(G, {
+        if ((e = run_rows<LL, +1>(a, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, +1>(b, P.stream)) != cudaSuccess) return e;
+        if ((e = run_cols<LL, +1>(c, P.stream)) != cudaSuccess) return e;
+    });
+    P.launches += 3;
+    return e;
+}
+
 // ---------------------------------------------------------------------------
 // Forward projector (eq. forward-projector), transform half of the type-2 NUFFT: the
 // volume times (-1)^n / phihat(n / 2N) per axis (dec_r; the sign centres the fine
@@ -1097,10 +1117,11 @@ struct PColsZOp {
     __device__ __forceinline__ void store(int, int k, int i, float2 v) const { u[(size_t)k * n_inner + i] = v; }
 };
 
-// d = 1 / ((max(kappa, 0) + floor) N^3), floor = lam_eff or 1e-6 kappa(0)
-__global__ void k_pc_diag(const float2* __restrict__ u, float* __restrict__ d, long long total, float lam) {
+// d = 1 / ((max(kappa, 0) + floor) N^3), floor = lam_eff (device lam[0]) or 1e-6 kappa(0)
+__global__ void k_pc_diag(const float2* __restrict__ u, float* __restrict__ d, long long total, const float* lam_p,
+                          float n3) {
+    const float lam = lam_p[0];
     const float floor_v = lam > 0.0f ? lam : 1e-6f * fmaxf(u[0].x, 1e-30f);
-    const float n3 = (float)d[total];   // N^3 stashed past the end by the launcher
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
         d[i] = 1.0f / ((fmaxf(u[i].x, 0.0f) + floor_v) * n3);
 }
@@ -1139,10 +1160,7 @@ cudaError_t launch_chan_spectrum(Plan& P) {
 cudaError_t launch_pc_build_circulant(Plan& P) {
     const long long total = (long long)P.N * P.N * (P.N / 2 + 1);
     const float n3 = (float)P.N * (float)P.N * (float)P.N;
-    cudaError_t e = cudaMemcpyAsync(P.ws.pc_diag + total, &n3, sizeof(float), cudaMemcpyHostToDevice, P.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
-    if (e != cudaSuccess) return e;
-    k_pc_diag<<<P.num_sms * 4, 256, 0, P.stream>>>(P.ws.t1, P.ws.pc_diag, total, (float)P.lam_eff);
+    k_pc_diag<<<P.num_sms * 4, 256, 0, P.stream>>>(P.ws.t1, P.ws.pc_diag, total, P.ws.lam, n3);
     P.launches += 1;
     return cudaGetLastError();
 }

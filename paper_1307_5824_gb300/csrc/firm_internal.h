@@ -75,6 +75,7 @@ struct Workspace {
     float2* tw_4n = nullptr;
     float* dec_k = nullptr;         // deconvolution factors, Ker (2N) and A*b (N)
     float* dec_r = nullptr;
+    float* dec_r4 = nullptr;        // A*b from the 4N grid (fused form): (-1)^n / phihat(n / 4N)
     // spreading
     float2* samples = nullptr;      // [m][t] h b (t = 0 halved)
     uint32_t* count = nullptr;      // per brick
@@ -111,6 +112,7 @@ struct Workspace {
     double* hist = nullptr;
     CgState* cg = nullptr;
     float* lam = nullptr;           // device: [0] lam_eff, [1] Ker(0) of the last kernel
+    float* axis = nullptr;          // device: principal viewing axis of the last kernel (3 floats)
     // FP64 CG mode only (FIRM_FLAG_FP64_CG; empty otherwise)
     double2* tw64 = nullptr;        // exp(-2 pi i k / 2N), k < N
     double* khat64 = nullptr;       // Re K-hat, full (2N)^3
@@ -132,7 +134,6 @@ struct Plan {
     size_t max_work = 0;
     int chunk = kChunk;             // points per spreading work item (kMinChunk..kChunk)
     KbPoly poly{};
-    double lam_eff = 0.0;
     double mu = 0.0;                // high-frequency damping weight (firm_set_damping)
     float h2_max = 1.0f;           // largest kernel-channel weight (bounds the fixed-point scale)
     bool have_kernel = false, have_rhs = false;
@@ -146,8 +147,6 @@ struct Plan {
     long long launches = 0;         // kernels launched by this plan
     int pc_mode = 0;                // FIRM_PRECOND_*
     bool pc_ready = false;          // pc_diag built for the current K-hat and mode
-    float pc_axis[3] = {0, 0, 1};   // principal viewing axis of the last firm_kernel
-    float ker0 = 1.0f;              // Ker(0) of the last firm_kernel
     int last_M = 0;                 // images of the last firm_kernel
     int bin_M = -1;                 // images of the last firm_bin (its ids and items still held); -1 none
     bool bin_kc = true;             // channel of the last firm_bin (true: kernel, 4N grid)
@@ -184,6 +183,10 @@ cudaError_t launch_bin(Plan& P, int M, bool kernel_channel);
 cudaError_t launch_spread(Plan& P, int M, bool kernel_channel);        // clear + spread
 cudaError_t launch_spread_clear(Plan& P, bool kernel_channel);          // zero the fine grid
 cudaError_t launch_spread_only(Plan& P, int M, bool kernel_channel);    // spread (grid cleared)
+// Both channels onto the 4N grid in one pass (clears the Ker and A*b grids first): the
+// points of the kernel channel's binning (launch_bin(P, M, true)), the A*b weights read
+// from ws.samples.  FIRM_FLAG_FUSED plans only.
+cudaError_t launch_spread_fused(Plan& P, int M);
 // One persistent launch spreading the binned points of n plans (same W) into their own
 // fine grids; each plan's grid cleared and its points binned beforehand.  args: device
 // array of n per-plan descriptors; item_off: device (n + 1) ints; queue: device int.
@@ -207,6 +210,7 @@ cudaError_t launch_interp(Plan& P, int M, const float2* ghat, float2* out, doubl
 cudaError_t launch_ker_transform(Plan& P);     // grid -> Ker half box
 cudaError_t launch_khat(Plan& P);              // Ker -> K-hat
 cudaError_t launch_rhs_transform(Plan& P);     // grid -> A*b
+cudaError_t launch_rhs_transform4(Plan& P);    // the fused form's 4N A*b grid -> A*b
 cudaError_t launch_lam_eff(Plan& P);           // ws.lam from Ker(0) on the device
 // Toeplitz apply y = Ker * x + lam_eff x (lam_eff read from ws.lam).  With cg != nullptr
 // the first pass forms p = r + beta p in place (x = p, r given) and the last pass
@@ -223,6 +227,8 @@ cudaError_t launch_pc_build_circulant(Plan& P);  // pc_diag = 1 / ((kappa + lam_
 // ---- launchers (lpre.cu) ----
 cudaError_t launch_view_axis(Plan& P, const double* R, int M);
 cudaError_t launch_pc_features(Plan& P, int M, float* hist);
+// hist <- hist / sum(hist); x (nullable) <- log(1024 hist + 1e-3), the network input
+cudaError_t launch_pc_normalize(Plan& P, float* hist, float* x);
 cudaError_t launch_pc_target_sums(Plan& P, double* s1, double* s2);
 cudaError_t launch_pc_bin_counts(Plan& P, double* s1, double* s2);     // grid frequencies per bin
 cudaError_t launch_pc_from_table(Plan& P, const float* table);

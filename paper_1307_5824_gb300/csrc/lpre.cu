@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(1024) k_view_moment(const double* __restrict__
 // and adds them to the block's histogram once.
 __global__ void __launch_bounds__(256) k_pc_features(const ImgGeom* __restrict__ geom, const int32_t* __restrict__ htab,
                                                      const int32_t* __restrict__ gid, const float* __restrict__ h2,
-                                                     int M, int nH, int n_ctf, float halfN, float a1, float a2, float a3,
-                                                     float* __restrict__ hist) {
+                                                     int M, int nH, int n_ctf, float halfN,
+                                                     const float* __restrict__ axis, float* __restrict__ hist) {
+    const float a1 = axis[0], a2 = axis[1], a3 = axis[2];
     __shared__ float s_h[kBins];
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_h[i] = 0.0f;
     __syncthreads();
@@ -99,8 +100,12 @@ __global__ void __launch_bounds__(256) k_pc_features(const ImgGeom* __restrict__
 
 // per-bin sums of (kappa + lam) and (kappa + lam)^2 over the half spectrum of the
 // circulant (weight 2 for the interior k1 columns whose mirror is not stored)
-__global__ void __launch_bounds__(256) k_pc_target_sums(const float2* __restrict__ u, int N, float lam, float a1, float a2,
-                                                        float a3, double* __restrict__ s1, double* __restrict__ s2) {
+// lam: device lam_eff (lam[0]); nullptr counts frequencies (u == nullptr too)
+__global__ void __launch_bounds__(256) k_pc_target_sums(const float2* __restrict__ u, int N, const float* __restrict__ lam_p,
+                                                        const float* __restrict__ axis, double* __restrict__ s1,
+                                                        double* __restrict__ s2) {
+    const float a1 = axis[0], a2 = axis[1], a3 = axis[2];
+    const float lam = lam_p ? lam_p[0] : 0.0f;
     __shared__ float sh1[kBins], sh2[kBins];
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) { sh1[i] = 0.0f; sh2[i] = 0.0f; }
     __syncthreads();
@@ -123,8 +128,12 @@ __global__ void __launch_bounds__(256) k_pc_target_sums(const float2* __restrict
 }
 
 // d(q) = exp(table[bin(q)]) / (Ker(0) N^3) on the half spectrum
-__global__ void __launch_bounds__(256) k_pc_from_table(const float* __restrict__ table, int N, float scale, float a1,
-                                                       float a2, float a3, float* __restrict__ d) {
+// d(q) = exp(table[bin(q)]) / (Ker(0) N^3), Ker(0) = lam[1] on the device (1 if not positive)
+__global__ void __launch_bounds__(256) k_pc_from_table(const float* __restrict__ table, int N, const float* __restrict__ lam,
+                                                       const float* __restrict__ axis, float* __restrict__ d) {
+    const float a1 = axis[0], a2 = axis[1], a3 = axis[2];
+    const float k0 = lam[1] > 0.0f ? lam[1] : 1.0f;
+    const float scale = 1.0f / (k0 * (float)N * (float)N * (float)N);
     const int H = N / 2 + 1;
     const long long total = (long long)N * N * H;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
@@ -135,20 +144,21 @@ __global__ void __launch_bounds__(256) k_pc_from_table(const float* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Principal axis (host): Jacobi eigenvalue iterations on the symmetric 3x3 moment.
+// Principal axis: Jacobi eigenvalue iterations on the symmetric 3x3 moment, on the
+// device (one thread), so that firm_kernel needs no host round trip.
 // ---------------------------------------------------------------------------
-static void principal_axis(const double* S, float* a) {
+__device__ static void principal_axis(const double* S, float* a) {
     double A[3][3], V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) A[i][j] = 0.5 * (S[3 * i + j] + S[3 * j + i]);
     for (int sweep = 0; sweep < 50; ++sweep) {
-        double off = std::fabs(A[0][1]) + std::fabs(A[0][2]) + std::fabs(A[1][2]);
-        if (off < 1e-15 * (std::fabs(A[0][0]) + std::fabs(A[1][1]) + std::fabs(A[2][2]) + 1e-300)) break;
+        double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+        if (off < 1e-15 * (fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]) + 1e-300)) break;
         for (int p = 0; p < 2; ++p)
             for (int q = p + 1; q < 3; ++q) {
                 if (A[p][q] == 0.0) continue;
-                const double th = 0.5 * std::atan2(2 * A[p][q], A[q][q] - A[p][p]);
-                const double c = std::cos(th), s = std::sin(th);
+                const double th = 0.5 * atan2(2 * A[p][q], A[q][q] - A[p][p]);
+                const double c = cos(th), s = sin(th);
                 for (int k = 0; k < 3; ++k) {       // A <- J^T A J
                     const double akp = A[k][p], akq = A[k][q];
                     A[k][p] = c * akp - s * akq;
@@ -169,20 +179,20 @@ static void principal_axis(const double* S, float* a) {
     int best = 0;
     for (int i = 1; i < 3; ++i)
         if (A[i][i] > A[best][best]) best = i;
-    const double n = std::sqrt(V[0][best] * V[0][best] + V[1][best] * V[1][best] + V[2][best] * V[2][best]);
+    const double n = sqrt(V[0][best] * V[0][best] + V[1][best] * V[1][best] + V[2][best] * V[2][best]);
     for (int i = 0; i < 3; ++i) a[i] = (float)(V[i][best] / (n > 0 ? n : 1.0));
+}
+
+__global__ void k_view_axis(const double* __restrict__ S, float* __restrict__ axis) {
+    principal_axis(S, axis);
 }
 
 cudaError_t launch_view_axis(Plan& P, const double* R, int M) {
     double* tmp = P.ws.red_b;      // 9 doubles of scratch
     k_view_moment<<<1, 1024, 0, P.stream>>>(R, M, tmp);
-    P.launches += 1;
-    double S[9];
-    cudaError_t e = cudaMemcpyAsync(S, tmp, sizeof(S), cudaMemcpyDeviceToHost, P.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
-    if (e != cudaSuccess) return e;
-    principal_axis(S, P.pc_axis);
-    return cudaSuccess;
+    k_view_axis<<<1, 1, 0, P.stream>>>(tmp, P.ws.axis);
+    P.launches += 2;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pc_features(Plan& P, int M, float* hist) {
@@ -190,7 +200,38 @@ cudaError_t launch_pc_features(Plan& P, int M, float* hist) {
     if (e != cudaSuccess || M <= 0) return e;
     const dim3 grid((P.nH + 255) / 256, (unsigned)(M < 256 ? M : 256));
     k_pc_features<<<grid, 256, 0, P.stream>>>(P.ws.geom, P.ws.htab, P.cur_gid, P.ws.h2, M, P.nH, P.n_ctf, 0.5f * P.N,
-                                              P.pc_axis[0], P.pc_axis[1], P.pc_axis[2], hist);
+                                              P.ws.axis, hist);
+    P.launches += 1;
+    return cudaGetLastError();
+}
+
+// Features f_b = h_b / sum_b h_b (the h^2-weighted share of the samples in every bin)
+// and, with x != nullptr, the network input x_b = log(1024 f_b + 1e-3).  One block of
+// kBins threads; the sum is a fixed-order tree, so the result is deterministic.
+__global__ void __launch_bounds__(kBins) k_pc_normalize(float* __restrict__ hist, float* __restrict__ x) {
+    __shared__ double s_w[kBins / 32];
+    const int i = threadIdx.x, lane = i & 31, wid = i >> 5;
+    const float h = hist[i];
+    double v = h;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) s_w[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = s_w[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s_w[0] = v;
+    }
+    __syncthreads();
+    const double tot = s_w[0];
+    const float f = tot > 0.0 ? (float)((double)h / tot) : 0.0f;
+    hist[i] = f;
+    if (x) x[i] = logf((float)kBins * f + 1e-3f);
+}
+
+cudaError_t launch_pc_normalize(Plan& P, float* hist, float* x) {
+    k_pc_normalize<<<1, kBins, 0, P.stream>>>(hist, x);
     P.launches += 1;
     return cudaGetLastError();
 }
@@ -199,8 +240,7 @@ cudaError_t launch_pc_target_sums(Plan& P, double* s1, double* s2) {
     cudaError_t e = cudaMemsetAsync(s1, 0, sizeof(double) * kBins, P.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, sizeof(double) * kBins, P.stream);
     if (e != cudaSuccess) return e;
-    k_pc_target_sums<<<P.num_sms * 2, 256, 0, P.stream>>>(P.ws.t1, P.N, (float)P.lam_eff, P.pc_axis[0], P.pc_axis[1],
-                                                          P.pc_axis[2], s1, s2);
+    k_pc_target_sums<<<P.num_sms * 2, 256, 0, P.stream>>>(P.ws.t1, P.N, P.ws.lam, P.ws.axis, s1, s2);
     P.launches += 1;
     return cudaGetLastError();
 }
@@ -210,16 +250,13 @@ cudaError_t launch_pc_bin_counts(Plan& P, double* s1, double* s2) {
     cudaError_t e = cudaMemsetAsync(s1, 0, kBins * sizeof(double), P.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, kBins * sizeof(double), P.stream);
     if (e != cudaSuccess) return e;
-    k_pc_target_sums<<<P.num_sms * 2, 256, 0, P.stream>>>(nullptr, P.N, 0.0f, P.pc_axis[0], P.pc_axis[1],
-                                                          P.pc_axis[2], s1, s2);
+    k_pc_target_sums<<<P.num_sms * 2, 256, 0, P.stream>>>(nullptr, P.N, nullptr, P.ws.axis, s1, s2);
     P.launches += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_pc_from_table(Plan& P, const float* table) {
-    const float n3 = (float)P.N * (float)P.N * (float)P.N;
-    k_pc_from_table<<<P.num_sms * 4, 256, 0, P.stream>>>(table, P.N, 1.0f / (P.ker0 * n3), P.pc_axis[0], P.pc_axis[1],
-                                                         P.pc_axis[2], P.ws.pc_diag);
+    k_pc_from_table<<<P.num_sms * 4, 256, 0, P.stream>>>(table, P.N, P.ws.lam, P.ws.axis, P.ws.pc_diag);
     P.launches += 1;
     return cudaGetLastError();
 }

@@ -119,6 +119,22 @@ __device__ __forceinline__ void window_taps(const KbPoly& P, float f, float* w) 
     }
 }
 
+// Dither of the kernel channel's fixed-point rounding: a value in [-1/2, 1/2) fixed by
+// the point id (a 32-bit integer hash), added to every tap of the point before it is
+// rounded to an integer.  Rounding to nearest drops every tap below half a unit, and
+// the far taps of the window are that small: without the dither the kernel's sums come
+// out biased low (~1e-6 relative, a smooth error that moves a 10-iteration CG volume by
+// 1e-4 on the N=64 workload).  With it the rounding is unbiased, E[round(v + d)] = v
+// for d uniform, and its error is white (a 1e-6 white error in Ker moves that volume by
+// ~4e-7).
+__device__ __forceinline__ float point_dither(uint32_t id) {
+    uint32_t h = id * 2654435761u;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    return (float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f;
+}
+
 // Bricks: 8 x 8 x BZ cells (BZ = kBrickZk for the kernel channel, 8 for A*b).
 template <bool KC> struct Brick { static constexpr int BZ = KC ? kBrickZk : kBrick; };
 
@@ -470,7 +486,8 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
 // Spreading
 //
 // Level 1: int32 fixed point in shared memory, one native shared-memory atomic add
-// per tap (v * S rounded to nearest through the FMA with 1.5 * 2^23).  S is a power
+// per tap (v * S rounded to nearest through the FMA with 1.5 * 2^23; the kernel
+// channel adds the point's dither first, see point_dither).  S is a power
 // of two with max|w| * S <= 2^21 (A*b) or 2^20 (kernel), and level 1 is folded into
 // the FP32 level-2 region after every 512 (A*b) or 1024 (kernel) points of the block,
 // so a cell can never exceed 2^30.  Level 2 is added into the FP64 grid when the work
@@ -485,6 +502,7 @@ struct SpreadArgs {
     const int32_t* gid;
     const float* h2;          // kernel channel weights [group][t]
     const float2* samples_b;  // right-hand-side weights in scatter order
+    const float2* samples;    // fused form: the weights h b at [m][t]
     const uint16_t* perm;     // per payload position: the point's index in scatter order
     double* grid;             // G^3 real, or G^3 complex interleaved (re, im)
     int G, halfG, nb, nH, n_ctf;
@@ -509,9 +527,9 @@ __device__ __forceinline__ float2 point_weight(const SpreadArgs& a, bool cplx, i
 // block-wide barrier; with PPR points per thread a cell can receive at most 256 * PPR
 // taps between folds, so a tap is scaled to at most 2^30 / (256 * PPR): 2^21 for the
 // A*b channel (PPR 2) and 2^20 for the kernel channel (PPR 4, half the barriers; the
-// extra bit of rounding takes Ker's fixed-point error from ~6e-7 to ~1.2e-6, still
-// well below the window's own ~5e-6 at W=6; for A*b it would double the fixed-point
-// error to ~3e-6 for a 1% gain, so A*b keeps PPR 2).
+// extra bit of rounding is white noise under the dither, which CG does not amplify;
+// for A*b it would double the fixed-point error to ~3e-6 for a 1% gain, so A*b keeps
+// PPR 2).
 template <bool CPLX> struct SpreadRound { static constexpr int PPR = CPLX ? 2 : 4; static constexpr int kScaleBits = CPLX ? 21 : 20; };
 
 // One work item (a piece of one brick's points) into the brick's shared-memory region,
@@ -574,6 +592,7 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
             window_taps<W>(poly, p.f[1], wy);
             window_taps<W>(poly, p.f[2], wz);
             const float wr = wv.x * S, wi = wv.y * S;
+            const float dth = CPLX ? 0.0f : point_dither(id);
 #pragma unroll
             for (int dz = 0; dz < W; ++dz) {
                 const float az = wr * wz[dz], bzw = wi * wz[dz];
@@ -583,8 +602,12 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
                     int* row = lev1 + base + (dz * RG + dy) * RG;
 #pragma unroll
                     for (int dx = 0; dx < W; ++dx) {
-                        atomicAdd(row + dx, __float_as_int(fmaf(ayz, wx[dx], kMagic)) - kMagicBits);
-                        if (CPLX) atomicAdd(row + RG3 + dx, __float_as_int(fmaf(byz, wx[dx], kMagic)) - kMagicBits);
+                        if (CPLX) {
+                            atomicAdd(row + dx, __float_as_int(fmaf(ayz, wx[dx], kMagic)) - kMagicBits);
+                            atomicAdd(row + RG3 + dx, __float_as_int(fmaf(byz, wx[dx], kMagic)) - kMagicBits);
+                        } else {
+                            atomicAdd(row + dx, __float_as_int(__fadd_rn(fmaf(ayz, wx[dx], dth), kMagic)) - kMagicBits);
+                        }
                     }
                 }
             }
@@ -705,6 +728,166 @@ __global__ void k_batch_items(const SpreadArgs* __restrict__ desc, int n, int* _
     }
 }
 
+// ---------------------------------------------------------------------------
+// Both channels in one pass (the fused form of FIRM steps 2-3): the points of the
+// kernel channel's binning on the 4N grid (which needs the poses only, so it can run
+// while the images are still uploading) carry both weights, h^2 (eq. kernel) and h b
+// (eq. backprojection, read from the image DFT's [m][t] samples by point id), and every
+// window tap is formed once and added to three shared-memory planes (Ker; A*b real and
+// imaginary).  Level 2 goes to the FP64 Ker
+// grid (real, G^3) and the FP64 A*b grid (complex, G^3, right after it); A*b is then
+// read from the 4N grid (oversampling 4 for its N modes).  Fixed point as in
+// spread_piece: the kernel channel's scale comes from the largest h^2 of the CTF table,
+// the A*b scale from the piece's own largest |h b|; PPR points per thread between folds.
+// ---------------------------------------------------------------------------
+struct FusedRound { static constexpr int PPR = 2; static constexpr int kScaleBits = 21; };
+
+template <int W>
+__device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const KbPoly& poly, const int4 wk, int* lev1,
+                                                   float* lev2, float* s_red) {
+    constexpr int BZ = kBrickZk;
+    constexpr int RG = kBrick + W;
+    constexpr int RG3 = RG * RG * (BZ + W);
+    constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
+    constexpr int kMagicBits = 0x4B400000;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = wk.x;
+    const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
+    const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * BZ;
+    const uint32_t s0 = (uint32_t)wk.y + threadIdx.x;
+    const int my_n = wk.z > (int)threadIdx.x ? (wk.z - (int)threadIdx.x + kSpreadThreads - 1) / kSpreadThreads : 0;
+    // largest |h b| of the piece (the A*b scale)
+    float wmax = 0.0f;
+    for (int i = 0; i < my_n; ++i) {
+        const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
+        const float2 wv = __ldg(&a.samples[(size_t)(id >> kTBits) * a.nH + (id & ((1u << kTBits) - 1u))]);
+        wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (lane == 0) s_red[warp] = wmax;
+    __syncthreads();
+    wmax = s_red[0];
+#pragma unroll
+    for (int i = 1; i < kSpreadWarps; ++i) wmax = fmaxf(wmax, s_red[i]);
+    constexpr int PPR = FusedRound::PPR, SB = FusedRound::kScaleBits;
+    const int rounds = (((wk.z + kSpreadThreads - 1) / kSpreadThreads) + PPR - 1) / PPR;
+    int ek = 0, eb = 0;
+    if (a.wmax_fixed > 0.0f) frexpf(a.wmax_fixed, &ek);
+    if (wmax > 0.0f) frexpf(wmax, &eb);
+    const float Sk = ldexpf(1.0f, SB - ek), invSk = ldexpf(1.0f, ek - SB);
+    const float Sb = ldexpf(1.0f, SB - eb), invSb = ldexpf(1.0f, eb - SB);
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll 1
+        for (int q = 0; q < PPR; ++q) {
+            const int i = PPR * r + q;
+            if (i >= my_n) continue;
+            const uint32_t pos = s0 + kSpreadThreads * i;
+            const uint32_t id = __ldg(&a.payload[pos]);
+            const int m = (int)(id >> kTBits);
+            const int t = (int)(id & ((1u << kTBits) - 1u));
+            const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
+            const int base = region_base<W, BZ>(p, lo0, lo1, lo2);
+            if (base < 0) {
+                atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
+                continue;
+            }
+            const int g = min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1);
+            const float wk2 = __ldg(&a.h2[(size_t)g * a.nH + t]) * Sk;
+            const float2 wv = __ldg(&a.samples[(size_t)m * a.nH + t]);
+            const float wr = wv.x * Sb, wi = wv.y * Sb;
+            const float dth = point_dither(id);
+            float wx[W], wy[W], wz[W];
+            window_taps<W>(poly, p.f[0], wx);
+            window_taps<W>(poly, p.f[1], wy);
+            window_taps<W>(poly, p.f[2], wz);
+#pragma unroll
+            for (int dz = 0; dz < W; ++dz) {
+                const float kz = wk2 * wz[dz], az = wr * wz[dz], bzw = wi * wz[dz];
+#pragma unroll
+                for (int dy = 0; dy < W; ++dy) {
+                    const float kyz = kz * wy[dy], ayz = az * wy[dy], byz = bzw * wy[dy];
+                    int* row = lev1 + base + (dz * RG + dy) * RG;
+#pragma unroll
+                    for (int dx = 0; dx < W; ++dx) {
+                        atomicAdd(row + dx, __float_as_int(__fadd_rn(fmaf(kyz, wx[dx], dth), kMagic)) - kMagicBits);
+                        atomicAdd(row + RG3 + dx, __float_as_int(fmaf(ayz, wx[dx], kMagic)) - kMagicBits);
+                        atomicAdd(row + 2 * RG3 + dx, __float_as_int(fmaf(byz, wx[dx], kMagic)) - kMagicBits);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * RG3; i += blockDim.x) {
+            const int v = lev1[i];
+            if (v != 0) {
+                lev2[i] = fmaf((float)v, i < RG3 ? invSk : invSb, lev2[i]);
+                lev1[i] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    // level 2 into the FP64 grids (periodic wrap) and cleared
+    const int o0 = lo0 - W / 2, o1 = lo1 - W / 2, o2 = lo2 - W / 2;
+    double* gk = a.grid;
+    double* gb = a.grid + (size_t)a.G * a.G * a.G;
+    for (int i = threadIdx.x; i < RG3; i += blockDim.x) {
+        const float vk = lev2[i], vr = lev2[RG3 + i], vi = lev2[2 * RG3 + i];
+        lev2[i] = 0.0f;
+        lev2[RG3 + i] = 0.0f;
+        lev2[2 * RG3 + i] = 0.0f;
+        if (vk == 0.0f && vr == 0.0f && vi == 0.0f) continue;
+        const int rx = i % RG, ry = (i / RG) % RG, rz = i / (RG * RG);
+        int gx = o0 + rx, gy = o1 + ry, gz = o2 + rz;
+        gx += (gx < 0) ? a.G : 0;
+        gx -= (gx >= a.G) ? a.G : 0;
+        gy += (gy < 0) ? a.G : 0;
+        gy -= (gy >= a.G) ? a.G : 0;
+        gz += (gz < 0) ? a.G : 0;
+        gz -= (gz >= a.G) ? a.G : 0;
+        const size_t cell = ((size_t)gz * a.G + gy) * a.G + gx;
+        if (vk != 0.0f) atomicAdd(&gk[cell], (double)vk);
+        if (vr != 0.0f) atomicAdd(&gb[2 * cell], (double)vr);
+        if (vi != 0.0f) atomicAdd(&gb[2 * cell + 1], (double)vi);
+    }
+    __syncthreads();
+}
+
+template <int W>
+__global__ void __launch_bounds__(kSpreadThreads) k_spread_fused(const SpreadArgs a) {
+    constexpr int R3 = (kBrick + W) * (kBrick + W) * (kBrickZk + W);
+    extern __shared__ int sm_i[];
+    int* lev1 = sm_i;                                          // 3 * R3 int32
+    float* lev2 = reinterpret_cast<float*>(sm_i + 3 * R3);     // 3 * R3 float
+    __shared__ int s_item;
+    __shared__ float s_red[kSpreadWarps];
+    for (int i = threadIdx.x; i < 6 * R3; i += blockDim.x) sm_i[i] = 0;
+    const int n_work = a.counters[0];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[1], 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_work) break;
+        spread_piece_fused<W>(a, a.poly, a.work[item], lev1, lev2, s_red);
+    }
+}
+
+template <int W>
+static cudaError_t spread_fused_w(Plan& P, const SpreadArgs& a) {
+    constexpr int R3 = (kBrick + W) * (kBrick + W) * (kBrickZk + W);
+    const size_t smem = sizeof(int) * 6 * R3;
+    cudaError_t e = cudaFuncSetAttribute(k_spread_fused<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_fused<W>, kSpreadThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    k_spread_fused<W><<<P.num_sms * per_sm, kSpreadThreads, smem, P.stream>>>(a);
+    P.launches += 1;
+    return cudaGetLastError();
+}
+
 template <int W, bool CPLX>
 static size_t spread_smem() {
     constexpr int R3 = (kBrick + W) * (kBrick + W) * (Brick<!CPLX>::BZ + W);
@@ -752,6 +935,7 @@ static SpreadArgs spread_args(Plan& P, bool kc) {
     a.gid = P.cur_gid;
     a.h2 = w.h2;
     a.samples_b = w.samples_b;
+    a.samples = w.samples;
     a.perm = w.perm;
     a.grid = w.grid;
     a.G = G;
@@ -786,6 +970,19 @@ cudaError_t launch_spread(Plan& P, int M, bool kc) {
     cudaError_t e = launch_spread_clear(P, kc);
     if (e != cudaSuccess) return e;
     return launch_spread_only(P, M, kc);
+}
+
+cudaError_t launch_spread_fused(Plan& P, int M) {
+    const size_t cells = (size_t)P.Gk * P.Gk * P.Gk;
+    cudaError_t e = cudaMemsetAsync(P.ws.grid, 0, sizeof(double) * 3 * cells, P.stream);
+    if (e != cudaSuccess || M <= 0) return e;
+    SpreadArgs a = spread_args(P, true);
+    switch (P.p.W) {
+        case 6: return spread_fused_w<6>(P, a);
+        case 7: return spread_fused_w<7>(P, a);
+        case 8: return spread_fused_w<8>(P, a);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 size_t spread_batch_desc_bytes() { return sizeof(SpreadArgs); }

@@ -40,11 +40,6 @@ def random_rotations(M: int, rng: np.random.Generator) -> np.ndarray:
     return R[rng.permutation(M)]
 
 
-def net_input(feat: np.ndarray) -> np.ndarray:
-    """x_b = log(1024 f_b + 1e-3)."""
-    return np.log(NBINS * np.asarray(feat, np.float64) + 1e-3).astype(np.float32)
-
-
 def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3000), device="cuda:0",
              defocus_um=DEFOCUS_UM, max_groups: int = 4, residual: bool = False):
     """(X, T): network inputs and targets of n_kernels method-generated kernels; each
@@ -58,7 +53,6 @@ def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3
     rec = Reconstructor(N, m_range[1], groups=groups, W=6, lam=1e-3, device=device)
     X = np.empty((n_kernels, NBINS), np.float32)
     T = np.empty((n_kernels, NBINS), np.float32)
-    f = np.empty(NBINS, np.float32)
     t = np.empty(NBINS, np.float32)
     for i in range(n_kernels):
         M = int(rng.integers(m_range[0], m_range[1] + 1))
@@ -66,12 +60,11 @@ def generate(n_kernels: int = 2000, N: int = 64, seed: int = 51, m_range=(500, 3
         sub = rng.choice(len(defocus_um), int(rng.integers(1, min(max_groups, len(defocus_um)) + 1)), replace=False)
         gid = sub[rng.integers(0, len(sub), M)].astype(np.int32)
         rec.kernel(np.ascontiguousarray(R.reshape(M, 9)), gid, M=M)
-        rec.pc_features(f)
+        rec.pc_net_input(X[i])
         if residual:
             rec.pc_residual_target(t)
         else:
             rec.pc_target(t)
-        X[i] = net_input(f)
         T[i] = t
     rec.close()
     return X, T
@@ -146,9 +139,9 @@ def predict(params: torch.Tensor, X: np.ndarray, bf16: bool = True) -> np.ndarra
 def apply_learned(rec: Reconstructor, params: torch.Tensor, bf16: bool = True, residual: bool = False) -> np.ndarray:
     """Features of the plan's last kernel -> network (+ the density baseline when the
     network was trained on residuals) -> FIRM_PRECOND_TABLE.  Returns the table."""
-    f = np.empty(NBINS, np.float32)
-    rec.pc_features(f)
-    out = predict(params, net_input(f)[None], bf16=bf16)[0]
+    x = np.empty(NBINS, np.float32)
+    rec.pc_net_input(x)
+    out = predict(params, x[None], bf16=bf16)[0]
     if residual:
         rec.set_precond_residual(np.ascontiguousarray(out))
     else:

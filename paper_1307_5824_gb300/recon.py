@@ -13,11 +13,13 @@ class Reconstructor:
 
     def __init__(self, N: int, M: int, groups=None, W: int = 6, lam: float = 0.0,
                  lambda_mode: int = L.FIRM_LAMBDA_RELATIVE, img_dtype: int = L.FIRM_IMG_F32,
-                 device="cuda:0", stream=None, flags: int = 0):
+                 device="cuda:0", stream=None, flags: int = 0, fused: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("the FIRM CUDA path needs a CUDA device")
         self.device = torch.device(device)
         table = np.zeros((0, 6)) if groups is None else np.asarray(groups, float).reshape(-1, 6)
+        if fused:
+            flags |= L.FIRM_FLAG_FUSED
         self.params = L.make_params(N, M, table.shape[0], W, 2.0, lam, lambda_mode, 0, img_dtype, flags)
         self._groups = L.make_groups(table)
         self.ws_bytes = L.firm_workspace_size(self.params)
@@ -35,6 +37,10 @@ class Reconstructor:
 
     def backproject(self, images, shifts, R, group=None, rhs_out=None, M=None):
         L.firm_backproject(self.plan, self.M if M is None else M, images, shifts, R, group, rhs_out)
+
+    def kernel_backproject(self, images, shifts, R, group=None, khat_out=None, rhs_out=None, M=None):
+        """Steps 1-3 with both spreading channels in one pass (plans made with fused=True)."""
+        L.firm_kernel_backproject(self.plan, self.M if M is None else M, images, shifts, R, group, khat_out, rhs_out)
 
     def stage_images(self, images, M=None):
         """Starts the upload of host `images` (pinned, M x N x N) into a device buffer
@@ -81,6 +87,10 @@ class Reconstructor:
 
     def pc_features(self, out):
         L.firm_pc_features(self.plan, out)
+
+    def pc_net_input(self, out):
+        """The learned network's input, log(1024 f + 1e-3) of the features (on the device)."""
+        L.firm_pc_net_input(self.plan, out)
 
     def pc_target(self, out):
         L.firm_pc_target(self.plan, out)

@@ -56,11 +56,11 @@ def test_forward_projector_matches_oracle(F, N, M, W):
     got = got[..., 0] + 1j * got[..., 1]
     e = rel(got, ref)
     print(f"A V N={N} M={M} W={W}: rel err {e:.3e}")
-    assert e <= (1.5e-5 if W == 6 else 1e-5)
+    assert e <= 1e-5
     # host arrays in and out through the same entry point
     out_h = np.empty((M, H.shape[0], 2), np.float32)
     F._lib.firm_forward(rec.plan, M, V, inp["R"].reshape(M, 9).copy(), inp["group_id"], out_h)
-    assert rel(out_h[..., 0] + 1j * out_h[..., 1], ref) <= (1.5e-5 if W == 6 else 1e-5)
+    assert rel(out_h[..., 0] + 1j * out_h[..., 1], ref) <= 1e-5
     rec.close()
 
 

@@ -142,4 +142,6 @@ def test_training_lowers_loss_and_preconditioners_converge(F):
     st, its["learned"] = rec.cg_solve(x, 800, rel_tol=1e-4)
     assert st == 0
     print("iterations", its)
+    # what the trained network gains over the method without it (plain CG)
+    assert its["learned"] <= 0.8 * its["none"]
     rec.close()

@@ -68,7 +68,7 @@ def test_kernel_and_khat_match_oracle(F, N, M, W, cfg):
     Ker = O.kernel(inp["R"], h, K, N)
     e_ker = rel(ker.cpu().numpy()[:, :, :N], _ker_half_from_oracle(Ker, N))
     e_kh = rel(khat.cpu().numpy(), O.khat_half(Ker.real))
-    tol = 1e-5 if W >= 7 else 1.5e-5
+    tol = 1e-5
     print(f"Ker N={N} M={M} W={W}: rel err Ker {e_ker:.3e} K-hat {e_kh:.3e}")
     assert e_ker <= tol, e_ker
     assert e_kh <= tol, e_kh
@@ -107,7 +107,7 @@ def test_backprojection_matches_oracle(F, N, M, W, dtype):
     s = smp.cpu().numpy()
     assert rel(s[..., 0] + 1j * s[..., 1], bH) <= 2e-6
     ref = O.backproject(img64, inp["shifts"], inp["R"], h, K)
-    tol = 1e-5 if W >= 7 else 1.5e-5
+    tol = 1e-5
     e_rhs = rel(rhs.cpu().numpy(), ref)
     print(f"A*b N={N} M={M} W={W} {dtype}: rel err {e_rhs:.3e}")
     assert e_rhs <= tol
@@ -138,14 +138,15 @@ def test_toeplitz_apply_matches_oracle(F):
     rec.close()
 
 
-@pytest.mark.parametrize("W,tol", [(7, 2e-4), (6, 3e-4)])
+@pytest.mark.parametrize("W,tol", [(6, 1e-4), (7, 2e-4)])
 def test_cg_config1_matches_oracle(F, W, tol):
     """FIRM on the N=32 workload: 200 noiseless Haar views, no CTF, lam=0, 10 CG iterations;
-    the volume vs the oracle's after the same count, default (FP32) path.  The FP32 FFTs
-    of the Toeplitz apply alone move this iterate by ~8e-5 (test_c1_fp32_fft_drift
-    measures it with a library FFT), and the window's ~5e-6 A*b error at W=6 adds ~1e-4
-    (x21, test_c1_volume_sensitivity_to_rhs_perturbation): gates 2e-4 (W=7) and 3e-4
-    (W=6).  The FP64 CG mode meets 1e-4 (test_cg_config1_fp64_mode_matches_oracle)."""
+    the volume vs the oracle's after the same count, default (FP32) path.  At the
+    workload's own window width (W=6) the gate is 1e-4 (measured 4.2e-5).  At W=7 the
+    FP32 FFTs of the Toeplitz apply move this lambda=0 iterate by ~1.3e-4 on their own
+    (the FP64 CG mode, same Ker and A*b, lands at 7e-6; a library FFT in FP32 moves it by
+    ~8e-5, test_c1_fp32_fft_drift), so that case keeps 2e-4; the FP64 CG mode meets 1e-4
+    at both widths (test_cg_config1_fp64_mode_matches_oracle)."""
     inp = synth.config_inputs("C1")
     N, M = inp["N"], inp["M"]
     K, h = _oracle_h(inp)
