@@ -86,6 +86,9 @@ def parse():
                          "RCT: random conical tilt (60 degrees), N=96, 10k images, SNR 1, with the FCR of the "
                          "solution inside and outside the missing cone")
     ap.add_argument("--batch", type=int, default=None, help="C4: reconstructions per batch (default 64)")
+    ap.add_argument("--channels", default="fused", choices=["fused", "separate"],
+                    help="fused: one binning and one spreading pass for Ker and A*b (firm_kernel_backproject); "
+                         "separate: firm_kernel then firm_backproject (timed beside the fused form either way)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--oracle-single", default=None, help=argparse.SUPPRESS)
@@ -243,12 +246,6 @@ def host_cpu_model():
     except Exception:
         pass
     return None
-
-
-def _features(rec):
-    f = np.empty(1024, np.float32)
-    rec.pc_features(f)
-    return f
 
 
 def cufft_comparison(rec, N, dev, stream, ours_apply_us, ours_fft_ker_ms):
@@ -534,10 +531,12 @@ def main():
     img = img_h.to(dev)
     inp["images"] = inp["images"][:5000].copy()     # the CPU-baseline sample keeps a few
 
-    rec = Reconstructor(N, M, groups=inp["groups"], W=args.W, lam=1e-3, img_dtype=L.FIRM_IMG_BF16, device=dev)
+    fused = args.channels == "fused"
+    rec = Reconstructor(N, M, groups=inp["groups"], W=args.W, lam=1e-3, img_dtype=L.FIRM_IMG_BF16, device=dev,
+                        fused=True)
     pc_modes = {"none": L.FIRM_PRECOND_NONE, "circulant": L.FIRM_PRECOND_CIRCULANT,
                 "binned": L.FIRM_PRECOND_BINNED, "learned": L.FIRM_PRECOND_TABLE}
-    net = None
+    infer = None
     train_info = None
     if args.precond == "learned":
         from paper_1307_5824_gb300 import learned
@@ -551,6 +550,8 @@ def main():
         train_info = {"kernels": int(len(X)), "N": args.train_N, "m_max": args.train_m_max,
                       "steps": args.train_steps, "gen_s": round(t_gen, 1), "loss": hist,
                       "val_mse_bf16": learned.evaluate(net, X[int(0.9 * len(X)):], T[int(0.9 * len(X)):], bf16=True)}
+        if not args.residual:
+            infer = learned.DeviceInference(net)
     elif args.precond != "physics":
         rec.set_precond(pc_modes[args.precond])
     x = torch.empty((N, N, N), dtype=torch.float32, device=dev)
@@ -558,22 +559,29 @@ def main():
 
     base_tab = np.empty(1024, np.float32)
     per_step_pc = {"on": True}          # the comparison run switches the per-step tables off
+    mode = {"fused": fused}
 
     def step(R_, g_, s_, im_, x_):
-        rec.kernel(R_, g_)
-        if per_step_pc["on"] and net is not None:
-            learned.apply_learned(rec, net, residual=args.residual)
+        if mode["fused"]:
+            rec.kernel_backproject(im_, s_, R_, g_)
+        else:
+            rec.kernel(R_, g_)
+        if per_step_pc["on"] and infer is not None:
+            infer.apply(rec)                           # on the device: no host round trip
+        elif per_step_pc["on"] and args.precond == "learned":
+            learned.apply_learned(rec, net, residual=True)
         elif per_step_pc["on"] and args.precond == "physics":
             rec.pc_baseline(base_tab)
             rec.set_precond_table(base_tab)
-        rec.backproject(im_, s_, R_, g_)
+        if not mode["fused"]:
+            rec.backproject(im_, s_, R_, g_)
         st, it = rec.cg_solve(x_, args.max_iter, rel_tol=REL_TOL, allow=(L.FIRM_ENOTCONV,))
         return st, it
 
     for _ in range(max(3, args.warmup)):
         st, iters = step(R, gid, sh, img, x)
     torch.cuda.synchronize(dev)
-    if net is not None:
+    if args.precond == "learned":
         # how far the network's table is from its own target for this workload's kernel
         xin = np.empty(1024, np.float32)
         rec.pc_net_input(xin)
@@ -585,33 +593,45 @@ def main():
             rec.pc_target(tgt)
         train_info["table_vs_target_mse"] = float(((tab - tgt) ** 2).mean())
 
-    # timed region: device-resident inputs; stage events recorded (no extra syncs)
-    rec.set_timing(True)
-    l0 = rec.launch_count()
-    stage_acc = {}
-    iters_list = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            torch.cuda.nvtx.range_push("firm_step")    # lets a profiler select the timed steps
-            st, iters = step(R, gid, sh, img, x)
-            torch.cuda.nvtx.range_pop()
-            iters_list.append(iters)
-            for k, v in rec.stage_times().items():
-                stage_acc[k] = stage_acc.get(k, 0.0) + v
-        e1.record(stream)
+    def timed(n_steps):
+        """n_steps steps between CUDA events on the plan's stream, stage events recorded
+        (no extra host synchronisation); returns (ms per step, stage ms, iterations,
+        launches, clocks)."""
+        rec.set_timing(True)
+        l0 = rec.launch_count()
+        acc, its = {}, []
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    ms_total = e0.elapsed_time(e1)
-    launches = rec.launch_count() - l0
-    rec.set_timing(False)
-    (ms_step,), (ms_per_recon,) = job_time([ms_total / args.steps], world, dev)
-    stages = {k: v / args.steps for k, v in stage_acc.items()}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            for _ in range(n_steps):
+                torch.cuda.nvtx.range_push("firm_step")    # lets a profiler select the timed steps
+                _, it_ = step(R, gid, sh, img, x)
+                torch.cuda.nvtx.range_pop()
+                its.append(it_)
+                for k, v in rec.stage_times().items():
+                    acc[k] = acc.get(k, 0.0) + v
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        rec.set_timing(False)
+        return (e0.elapsed_time(e1) / n_steps, {k: v / n_steps for k, v in acc.items()}, its,
+                rec.launch_count() - l0, clk.summary())
+
+    # timed region: device-resident inputs
+    ms_total, stages, iters_list, launches, clocks = timed(args.steps)
+    (ms_step,), (ms_per_recon,) = job_time([ms_total], world, dev)
+    # the other channel form, same preconditioner, for comparison
+    mode["fused"] = not fused
+    for _ in range(2):
+        step(R, gid, sh, img, x)
+    ms_other, stages_other, _, _, _ = timed(max(2, min(args.steps, 5)))
+    mode["fused"] = fused
+    step(R, gid, sh, img, x)
+    torch.cuda.synchronize(dev)
 
     # the true relative residual of the returned volume, ||A*b - (A*A + lam_eff) x|| / ||A*b||,
     # recomputed with one Toeplitz apply (the solve stops on the recurrence residual)
@@ -629,7 +649,7 @@ def main():
         x_h = torch.empty((N, N, N), dtype=torch.float32).pin_memory()
 
         # the two forms alternate step by step (same drift for both); the upload staged
-        # ahead overlaps the kernel channel
+        # ahead overlaps the binning (fused) or the kernel channel (separate)
         n_e2e = max(args.steps, 5)
         res = {False: 0.0, True: 0.0}
         for staged in (False, True):            # one untimed step of each form
@@ -649,9 +669,11 @@ def main():
                 res[staged] += time.perf_counter() - t0
         _, (serial_s, staged_s) = job_time([res[False] / n_e2e, res[True] / n_e2e], world, dev)
         res = {False: serial_s, True: staged_s}
-        h2d = 2 * R_h.numel() * 8 + 2 * g_h.numel() * 4 + s_h.numel() * 8 + img_h.numel() * 2
+        h2d = R_h.numel() * 8 + g_h.numel() * 4 + s_h.numel() * 8 + img_h.numel() * 2
         e2e = {"value": res[True], "unit": "s/recon", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(x_h.numel() * 4), "upload": "overlapped with the kernel channel",
+               "d2h_bytes_per_step": int(x_h.numel() * 4),
+               "upload": "staged ahead (firm_stage_images), overlapped with the binning" if fused else
+                         "staged ahead (firm_stage_images), overlapped with the kernel channel",
                "value_serial_upload": res[False]}
 
     # the same reconstruction with plain CG (the comparison the metric names)
@@ -660,22 +682,9 @@ def main():
         per_step_pc["on"] = False
         rec.set_precond(L.FIRM_PRECOND_NONE)
         for _ in range(2):
-            st, it_pl = step(R, gid, sh, img, x)
-        torch.cuda.synchronize(dev)
-        rec.set_timing(True)
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        it_plain = []
-        cg_plain = 0.0
-        p0.record(stream)
-        for _ in range(args.steps):
-            st, it_pl = step(R, gid, sh, img, x)
-            it_plain.append(it_pl)
-            cg_plain += rec.stage_times()["cg"]
-        p1.record(stream)
-        torch.cuda.synchronize(dev)
-        rec.set_timing(False)
-        plain = {"s_per_recon": p0.elapsed_time(p1) / args.steps / 1e3, "cg_iters": int(np.median(it_plain)),
-                 "cg_ms": cg_plain / args.steps}
+            step(R, gid, sh, img, x)
+        ms_plain, st_plain, it_plain, _, _ = timed(args.steps)
+        plain = {"s_per_recon": ms_plain / 1e3, "cg_iters": int(np.median(it_plain)), "cg_ms": st_plain["cg"]}
         per_step_pc["on"] = True
 
     if rank != 0:
@@ -685,18 +694,22 @@ def main():
 
     iters = int(np.median(iters_list))
     pts = M * nK
-    spread_ms = stages["spread_ker"] + stages["spread_rhs"]
     W = args.W
-    # roofline of the dominant kernel: the spreading kernel with the larger share.
-    # Work unit: one shared-memory atomic add (W^3 per half-disc point, x2 for the
-    # complex A*b channel).  Peak: 152 SMs x 32 lanes x 2.07 GHz (one warp-wide shared
-    # atomic per clock per SM) = 10.07e12 / s.
     nH = (nK + 1) // 2
-    dom = "spread_rhs" if stages["spread_rhs"] >= stages["spread_ker"] else "spread_ker"
-    atoms = M * nH * W ** 3 * (2 if dom == "spread_rhs" else 1)
+    # Spreading time of this form (the fused pass is stage 1; the separate channels are
+    # stages 1 and 6) and the roofline of the dominant kernel, the spreading pass.  Work
+    # unit: one shared-memory atomic add: W^3 per half-disc point for the kernel channel,
+    # 2 W^3 for A*b, 3 W^3 for the fused pass.  Peak: 152 SMs x 32 lanes x 2.07 GHz (one
+    # warp-wide shared atomic per clock per SM) = 10.07e12 / s.
+    spread_ms = stages["spread_ker"] + stages["spread_rhs"]
+    if fused:
+        dom, atoms, kname = "spread_ker", M * nH * W ** 3 * 3, f"k_spread_fused<{W}>"
+    else:
+        dom = "spread_rhs" if stages["spread_rhs"] >= stages["spread_ker"] else "spread_ker"
+        atoms = M * nH * W ** 3 * (2 if dom == "spread_rhs" else 1)
+        kname = f"k_spread<{W},{'complex' if dom == 'spread_rhs' else 'real'}>"
     peak = 152 * 32 * 2.07e9
     achieved = atoms / (stages[dom] * 1e-3)
-    kname = f"k_spread<{W},{'complex' if dom == 'spread_rhs' else 'real'}>"
     traffic = None
     prof = os.path.join(ROOT, "profiles", "spread_traffic.json")
     if os.path.exists(prof) and (N, M, W) == (128, 50000, 6):   # the figure is for this workload
@@ -704,6 +717,13 @@ def main():
             traffic = json.load(open(prof)).get(kname)
         except Exception:
             traffic = None
+    # the spreading pass against HBM (not its binding bound): algorithmic bytes = point ids
+    # and weights read + the FP64 fine grids written once
+    Gk, Gr = 4 * N, 2 * N
+    if fused:
+        spread_bytes = M * nH * (4 + 8) + 3 * Gk ** 3 * 8
+    else:
+        spread_bytes = M * nH * 4 + Gk ** 3 * 8 + M * nH * (4 + 8 + 2) + Gr ** 3 * 16
     hbm_peak = None
     try:
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -732,6 +752,11 @@ def main():
     toeplitz = {"applies_per_s": 1.0 / toep_s, "us_per_apply": toep_s * 1e6, "algorithmic_bytes": toep_bytes,
                 "achieved_gbs": toep_bytes / toep_s / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": toep_bytes / toep_s / 1e9 / hbm_peak, "peak_source": hbm_src}
+    del xa, ya
+    cufft = cufft_comparison(rec, N, dev, stream, toep_s * 1e6, stages.get("fft_ker", 0.0))
+    spread_hbm = {"algorithmic_bytes": int(spread_bytes), "achieved_gbs": spread_bytes / (spread_ms * 1e-3) / 1e9,
+                  "hbm_frac": spread_bytes / (spread_ms * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,
+                  "note": "not the binding bound: the spreading is bound by shared-memory atomic issue"}
 
     # the forward projector A of the solution (type-2 NUFFT at every half-disc sample)
     # and the data term |b - A x|^2 / |b|^2, device buffers, CUDA events
@@ -778,9 +803,12 @@ def main():
 
     cpu = None
     if not args.no_cpu and world == 1:                 # the oracle baseline: rank 0 at N=1 only
-        est, sample, parts = oracle_sample(inp, iters)
+        it_o = oracle_cg_iterations(args.workload) or (plain["cg_iters"] if plain else iters)
+        est, sample, parts = oracle_sample(inp, it_o)
         cpu = {"value": est, "unit": "s/recon", "cores": cores_used(), "kind": "oracle", "sample": sample,
-               "parts": parts}
+               "parts": parts, "cpu_model": host_cpu_model(), "threads": "gridding: OpenMP over all cores; "
+               "FFTs: scipy workers over all cores",
+               "single_core": oracle_single_core_times()}
 
     out = {
         "metric": METRIC, "value": ms_per_recon / 1e3, "unit": "s/recon", "n_gpus": world, "steps": args.steps,
@@ -788,12 +816,18 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(inp, W, args.precond, args.workload),
                    "N": N, "M": M, "W": W, "precond": args.precond,
-                   "l2": "inputs larger than L2: 1.64 GB BF16 images read and a 1.07 GB FP64 fine grid "
-                         "written every step"},
+                   "channels": args.channels,
+                   "l2": "inputs larger than L2: %.2f GB BF16 images read and %.2f GB of FP64 fine grids "
+                         "written every step" % (M * N * N * 2 / 1e9,
+                                                 (3 if fused else 1) * (4 * N) ** 3 * 8 / 1e9)},
+        "channels": args.channels,
         "spread_gpts_per_s": pts / (spread_ms * 1e-3) / 1e9,
-        "spread_gpts_per_s_by_channel": {"kernel": pts / (stages["spread_ker"] * 1e-3) / 1e9,
-                                         "rhs": pts / (stages["spread_rhs"] * 1e-3) / 1e9},
         "spread_points": pts,
+        "spread_hbm": spread_hbm,
+        ("s_per_recon_separate_channels" if fused else "s_per_recon_fused_channels"): ms_other / 1e3,
+        ("stage_ms_separate_channels" if fused else "stage_ms_fused_channels"):
+            {k: round(v, 4) for k, v in stages_other.items() if k != "cg_iters"},
+        "cufft_comparison": cufft,
         "toeplitz_applies_per_s": toeplitz["applies_per_s"],
         "toeplitz": toeplitz,
         "forward_projector": forward,
@@ -802,10 +836,12 @@ def main():
         "cg_iters_per_s": (iters / (stages["cg"] * 1e-3)) if stages.get("cg") else None,
         "cg_iters": iters,
         "true_rel_residual": true_rel_res,
-        # the kernel channel (binning and spreading of Ker, its transform, K-hat) depends
-        # on the poses only: a one-time precompute for a fixed pose set
-        "s_per_recon_without_precompute": (ms_per_recon - sum(stages.get(k, 0.0) for k in
-                                                              ("bin_ker", "spread_ker", "fft_ker", "khat"))) / 1e3,
+        # with separate channels the kernel channel (binning and spreading of Ker, its
+        # transform, K-hat) depends on the poses only: a one-time precompute for a fixed
+        # pose set
+        "s_per_recon_without_precompute": ((ms_other if fused else ms_per_recon) - sum(
+            (stages_other if fused else stages).get(k, 0.0) for k in ("bin_ker", "spread_ker", "fft_ker", "khat")))
+        / 1e3,
         "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},
         "roofline": {"kernel": kname, "bound": "alu",
                      "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tatomic/s",
@@ -814,7 +850,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "synth_s": round(t_syn, 1),
         "precond": args.precond,
         "learned_training": train_info,

@@ -159,6 +159,18 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
 int firm_kernel_backproject(firm_plan_t plan, int M, const void* images, const double* shifts,
                             const double* R, const int32_t* group, float* khat_out, float* rhs_out);
 
+/* Sums formed elsewhere, loaded into the plan.  Ker and A*b are sums over the images
+ * (eq. kernel, eq. backprojection; Section 3.4), so a reconstruction can be split by
+ * images: every process runs firm_kernel and firm_backproject (or
+ * firm_kernel_backproject) on its own images, copies out FIRM_OUT_KER and FIRM_OUT_RHS,
+ * the copies are summed across processes (one all-reduce), and each process loads the
+ * sums here.  ker_half (nullable): the Ker half box, 2N x 2N x (N+1) float32 as
+ * FIRM_OUT_KER; K-hat (eq. embedding_circulant, eq. circ1), lam_eff and the damping
+ * are formed from it as firm_kernel does.  rhs (nullable): A*b, N^3 float32.  Host or
+ * device memory.  The learned and binned preconditioners also use the viewing axis,
+ * which only firm_kernel forms from the poses.  FIRM_EINVAL if both are NULL. */
+int firm_load_sums(firm_plan_t plan, const float* ker_half, const float* rhs);
+
 /* Forward projector A (Section 3.1, eq. forward-projector; with eq. truncation's disc):
  *     (A V)_m(k) = h_m(|w_k|) sum_n V_n exp(-i <n, xi_{m,k}>),  xi = R_m^T (2 pi k / N, 0),
  * for the half disc of every image (the order of FIRM_OUT_SAMPLES: (0, k2) for

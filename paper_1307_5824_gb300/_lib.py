@@ -24,7 +24,7 @@ FIRM_BATCH_GRAPH, FIRM_BATCH_PERSISTENT = 1, 2
 FIRM_FLAG_FP64_CG, FIRM_FLAG_FUSED = 1, 2
 
 EXPORTED = [
-    "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_kernel_backproject",
+    "firm_workspace_size", "firm_plan", "firm_kernel", "firm_backproject", "firm_kernel_backproject", "firm_load_sums",
     "firm_stage_images", "firm_cg_solve",
     "firm_forward", "firm_data_residual", "firm_set_damping", "firm_solve_nonneg",
     "firm_toeplitz_apply", "firm_toeplitz_apply_static", "firm_set_precond", "firm_lambda_eff", "firm_copy_out", "firm_set_timing",
@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
     L.firm_kernel.argtypes = [vp, i, vp, vp, vp]
     L.firm_backproject.argtypes = [vp, i, vp, vp, vp, vp, vp]
     L.firm_kernel_backproject.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+    L.firm_load_sums.argtypes = [vp, vp, vp]
     L.firm_stage_images.argtypes = [vp, i, vp, vp, ctypes.c_size_t]
     L.firm_forward.argtypes = [vp, i, vp, vp, vp, vp]
     L.firm_set_damping.argtypes = [vp, d]
@@ -196,6 +197,10 @@ def firm_backproject(plan, M: int, images, shifts, R, group=None, rhs_out=None):
 def firm_kernel_backproject(plan, M: int, images, shifts, R, group=None, khat_out=None, rhs_out=None):
     _check(lib().firm_kernel_backproject(plan, M, _ptr(images), _ptr(shifts), _ptr(R), _ptr(group), _ptr(khat_out),
                                          _ptr(rhs_out)), "firm_kernel_backproject")
+
+
+def firm_load_sums(plan, ker_half=None, rhs=None):
+    _check(lib().firm_load_sums(plan, _ptr(ker_half), _ptr(rhs)), "firm_load_sums")
 
 
 def firm_stage_images(plan, M: int, images, staging, staging_bytes: int):

@@ -689,6 +689,7 @@ int firm_kernel_backproject(firm_plan_t plan, int M, const void* images, const d
     if (shifts) P.cur_shifts = stage(shifts, w.shifts, (size_t)M * 2, P.stream, e);
     else { if (e == cudaSuccess) e = cudaMemsetAsync(w.shifts, 0, sizeof(double) * 2 * (M > 0 ? M : 1), P.stream); P.cur_shifts = w.shifts; }
     FIRM_CK(e);
+    P.ev_used[5] = P.ev_used[6] = false;      // no separate A*b binning or spreading stage here
     const bool staged = M > 0 && P.staged_host == images && P.staged_M == M;
     // host images not staged ahead are copied into the workspace region the point ids
     // use, so they are transformed before the binning; otherwise the binning (poses
@@ -745,6 +746,34 @@ int firm_kernel_backproject(firm_plan_t plan, int M, const void* images, const d
     const int st = put_out_checked(P, khat_out, w.khat, sizeof(float) * 2 * P.N * 2 * P.N * (P.N + 1));
     if (st != FIRM_OK) return st;
     return put_out_checked(P, rhs_out, w.rhs, sizeof(float) * P.N * P.N * P.N);
+}
+
+int firm_load_sums(firm_plan_t plan, const float* ker_half, const float* rhs) {
+    if (!plan || (!ker_half && !rhs)) return FIRM_EINVAL;
+    Plan& P = plan->P;
+    Workspace& w = P.ws;
+    const size_t H3 = (size_t)2 * P.N * 2 * P.N * (P.N + 1), N3 = (size_t)P.N * P.N * P.N;
+    auto in = [&](const float* src, float* dst, size_t n) -> cudaError_t {
+        return cudaMemcpyAsync(dst, src, n * sizeof(float), is_device(src) ? cudaMemcpyDeviceToDevice
+                                                                          : cudaMemcpyHostToDevice, P.stream);
+    };
+    StageTimer tm(P);
+    if (ker_half) {
+        FIRM_CK(in(ker_half, w.ker, H3));
+        tm.start(3);
+        FIRM_CK(launch_khat(P));
+        FIRM_CK(launch_lam_eff(P));
+        if (P.p.flags & FIRM_FLAG_FP64_CG) FIRM_CK(launch_khat64(P));
+        FIRM_CK(launch_damping(P));
+        tm.stop();
+        P.have_kernel = true;
+        P.pc_ready = false;
+    }
+    if (rhs) {
+        FIRM_CK(in(rhs, w.rhs, N3));
+        P.have_rhs = true;
+    }
+    return FIRM_OK;
 }
 
 int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging, size_t staging_bytes) {

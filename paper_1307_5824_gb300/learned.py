@@ -147,3 +147,26 @@ def apply_learned(rec: Reconstructor, params: torch.Tensor, bf16: bool = True, r
     else:
         rec.set_precond_table(np.ascontiguousarray(out))
     return out
+
+
+class DeviceInference:
+    """The trained network applied to a plan without leaving the device: the features'
+    network input (firm_pc_net_input), the BF16 forward pass (firm_mlp_forward_bf16) and
+    the table (firm_set_precond_table) all read and write device buffers on the plan's
+    stream, so a reconstruction step never waits for the host."""
+
+    def __init__(self, params: torch.Tensor):
+        dev = params.device
+        self.params = params
+        self.pb = torch.empty(params.numel(), dtype=torch.bfloat16, device=dev)
+        self.x = torch.empty((1, NBINS), dtype=torch.float32, device=dev)
+        self.y = torch.empty((1, NBINS), dtype=torch.float32, device=dev)
+        self.work = torch.empty(L.firm_mlp_work_floats(1), dtype=torch.float32, device=dev)
+        L.firm_mlp_to_bf16(params, self.pb, torch.cuda.current_stream(dev).cuda_stream)
+
+    def apply(self, rec: Reconstructor):
+        s = rec.stream.cuda_stream
+        rec.pc_net_input(self.x)
+        L.firm_mlp_forward_bf16(self.pb, self.params, 1, self.x, self.y, self.work, s)
+        rec.set_precond_table(self.y)
+

@@ -42,6 +42,10 @@ class Reconstructor:
         """Steps 1-3 with both spreading channels in one pass (plans made with fused=True)."""
         L.firm_kernel_backproject(self.plan, self.M if M is None else M, images, shifts, R, group, khat_out, rhs_out)
 
+    def load_sums(self, ker_half=None, rhs=None):
+        """Ker half box and / or A*b summed elsewhere (image shards) -> K-hat, lam_eff."""
+        L.firm_load_sums(self.plan, ker_half, rhs)
+
     def stage_images(self, images, M=None):
         """Starts the upload of host `images` (pinned, M x N x N) into a device buffer
         held by this object; the next backproject with the same tensor reads it."""

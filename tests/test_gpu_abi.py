@@ -150,3 +150,54 @@ def test_fused_channels_match_oracle_and_separate_calls(F, N, M, W):
         rec.kernel_backproject(img, sh, R, g)
     assert e.value.code == L.FIRM_EINVAL
     rec.close()
+
+
+def test_image_shards_loaded_into_a_plan_match_the_whole_set(F):
+    """Two image shards spread by two plans (two processes' share of the images, run one
+    after the other on this one GPU), their Ker half boxes and A*b added, loaded into a
+    third plan with firm_load_sums: K-hat, lam_eff, A*b and the CG volume equal those of
+    one plan over all the images (Ker and A*b are sums over the images, Section 3.4)."""
+    L = F._lib
+    N, M = 32, 160
+    inp = synth.config_inputs("C2", M=M, N=N)
+    R, g, sh, img = (_dev(inp["R"].reshape(M, 9)), _dev(inp["group_id"]), _dev(inp["shifts"]),
+                     _dev(inp["images"]))
+    whole = F.Reconstructor(N, M, groups=inp["groups"], W=6, lam=1e-3)
+    kh_w = torch.empty(whole.half_shape(), dtype=torch.float32, device="cuda")
+    rhs_w = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    whole.kernel(R, g, khat_out=kh_w)
+    whole.backproject(img, sh, R, g, rhs_out=rhs_w)
+    ker_sum = torch.zeros(whole.half_shape(), dtype=torch.float32, device="cuda")
+    rhs_sum = torch.zeros((N, N, N), dtype=torch.float32, device="cuda")
+    for a, b in ((0, 70), (70, M)):
+        part = F.Reconstructor(N, b - a, groups=inp["groups"], W=6, lam=1e-3, fused=(a == 0))
+        k = torch.empty_like(ker_sum)
+        r = torch.empty_like(rhs_sum)
+        if a == 0:
+            part.kernel_backproject(img[a:b], sh[a:b], R[a:b], g[a:b])
+        else:
+            part.kernel(R[a:b], g[a:b])
+            part.backproject(img[a:b], sh[a:b], R[a:b], g[a:b])
+        part.copy_out(L.FIRM_OUT_KER, k)
+        part.copy_out(L.FIRM_OUT_RHS, r)
+        torch.cuda.synchronize()
+        ker_sum += k
+        rhs_sum += r
+        part.close()
+    loaded = F.Reconstructor(N, M, groups=inp["groups"], W=6, lam=1e-3)
+    kh_l = torch.empty_like(kh_w)
+    loaded.load_sums(ker_sum, rhs_sum)
+    loaded.copy_out(L.FIRM_OUT_KHAT, kh_l)
+    torch.cuda.synchronize()
+    assert _rel(kh_l.cpu().numpy(), kh_w.double().cpu().numpy()) <= 5e-6
+    assert abs(loaded.lambda_eff() - whole.lambda_eff()) <= 5e-6 * whole.lambda_eff()
+    x_w = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    x_l = torch.empty_like(x_w)
+    whole.cg_solve(x_w, 8)
+    loaded.cg_solve(x_l, 8)
+    assert _rel(x_l.cpu().numpy(), x_w.double().cpu().numpy()) <= 1e-4
+    with pytest.raises(L.FirmError) as e:
+        loaded.load_sums(None, None)
+    assert e.value.code == L.FIRM_EINVAL
+    whole.close()
+    loaded.close()

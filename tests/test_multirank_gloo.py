@@ -1,8 +1,10 @@
 """Two CPU ranks (gloo): Ker and A*b are sums over images (eq. kernel, eq. backprojection,
 Section 3.4), so splitting the images across ranks and adding the ranks' partial sums
-with one all-reduce gives the single-process result.  This is the additivity a
-sharded reconstruction would rely on; the benchmark's multi-GPU mode runs replicas
-and reduces only its timings, which the second test checks (max over ranks)."""
+with one all-reduce gives the single-process result.  The all-reduce is the product's
+own exchange step (paper_1307_5824_gb300.shard.allreduce_sums) applied to the oracle's
+per-rank sums; tests/test_gpu_abi.py loads such sums into a plan (firm_load_sums).  The
+benchmark's multi-GPU mode runs replicas and reduces only its timings, which the test
+also checks (max over ranks)."""
 import os
 import socket
 
@@ -33,8 +35,11 @@ def _worker(rank, world, port, out_path):
         a, b = rank * M // world, (rank + 1) * M // world
         ker = O.kernel(inp["R"][a:b], h[a:b], K, N).real
         rhs = O.backproject(inp["images"][a:b].astype(np.float64), inp["shifts"][a:b], inp["R"][a:b], h[a:b], K)
-        t = torch.from_numpy(np.concatenate([ker.ravel(), rhs.ravel()]))
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        # the product's exchange step (paper_1307_5824_gb300.shard), on CPU tensors
+        from paper_1307_5824_gb300 import shard
+        kt, rt = torch.from_numpy(ker.copy()), torch.from_numpy(rhs.copy())
+        shard.allreduce_sums(kt, rt)
+        t = torch.cat([kt.reshape(-1), rt.reshape(-1)])
         # timing reduction of the benchmark: max over ranks, whole job = world reconstructions
         import bench
         slow, per_recon = bench.job_time([10.0 + rank, 30.0 - rank], world, "cpu")
