@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--oracle-single", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--spread-only", action="store_true",
+                    help="profiling: the separate channels (firm_kernel + firm_backproject) twice, then the fused "
+                         "call twice, stage times printed; no benchmark line")
     return ap.parse_args()
 
 
@@ -456,6 +459,51 @@ def run_batched(args):
             h["x"].copy_(it["x"], non_blocking=True)
         torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / args.steps
+    # to relative residual 1e-4 (the learned preconditioner's target): the batch with the
+    # network (one forward pass over all plans), the batch with plain CG, and plain FIRM
+    # one reconstruction after another through the single-plan calls
+    from paper_1307_5824_gb300 import learned
+    t0 = time.perf_counter()
+    X, T = learned.generate(1000, N=64, m_range=(500, 3000), device=dev)
+    net, _ = learned.train(X, T, steps=2000, device=dev)
+    t_train = time.perf_counter() - t0
+    B.set_network(net)
+    tol_runs = {}
+    for name, is_learned in (("learned", True), ("plain", False)):
+        for r in recs:
+            r.set_precond(L.FIRM_PRECOND_NONE)
+        B.solve(MAX_ITER, REL_TOL, learned=is_learned)
+        B.wait(allow=(L.FIRM_ENOTCONV, L.FIRM_EBREAKDOWN))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        B.solve(MAX_ITER, REL_TOL, learned=is_learned)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        st_b, sts_b, its_b = B.wait(allow=(L.FIRM_ENOTCONV, L.FIRM_EBREAKDOWN))
+        bad = [(int(r.N), int(it["M"]), int(s_), int(i_)) for r, it, s_, i_ in zip(recs, items, sts_b, its_b) if s_ != 0]
+        tol_runs[name] = {"s_per_batch": dt, "recon_per_s": n / dt, "cg_iters_total": int(its_b.sum()),
+                          "cg_iters_median": int(np.median(its_b)), "all_converged": not bad,
+                          "not_converged (N, M, status, iterations)": bad[:8]}
+
+    def sequential_plain():
+        its_ = []
+        for r, it in zip(recs, items):
+            r.set_precond(L.FIRM_PRECOND_NONE)
+            r.kernel(it["R"], it["group"], M=it["M"])
+            r.backproject(it["images"], it["shifts"], it["R"], it["group"], M=it["M"])
+            its_.append(r.cg_solve(it["x"], MAX_ITER, rel_tol=REL_TOL, allow=(L.FIRM_ENOTCONV,))[1])
+        return its_
+    sequential_plain()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    its_seq = sequential_plain()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    tol_runs["plain_single_plan_sequential"] = {"s_per_batch": dt, "recon_per_s": n / dt,
+                                                "cg_iters_total": int(np.sum(its_seq))}
+    tol_runs["learned_vs_plain_sequential_speedup"] = dt / tol_runs["learned"]["s_per_batch"]
+    tol_runs["learned_vs_plain_batched_speedup"] = tol_runs["plain"]["s_per_batch"] / tol_runs["learned"]["s_per_batch"]
+    tol_runs["network"] = {"kernels": 1000, "N": 64, "steps": 2000, "train_s": round(t_train, 1)}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -474,6 +522,7 @@ def run_batched(args):
                             (sum(it["images"].numel() * 4 for it in items) / 1e9)},
            "tuned": tuned, "ms_no_graph": ms_nograph, "ms_sequential_single_plan": ms_seq,
            "speedup_vs_sequential": ms_seq / ms, "cg_status_ok": bool(st == 0),
+           "to_rel_res_1e-4": tol_runs,
            "gpu_launches": int(B.launch_count() * args.steps),
            "e2e": {"value": n / e2e_s, "unit": "recon/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
            "clocks": clk.summary(), "synth_s": round(t_syn, 1)}
@@ -483,6 +532,34 @@ def run_batched(args):
         r.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# profiling driver: the spreading stages alone
+# ---------------------------------------------------------------------------
+def run_spread_only(args):
+    import torch
+
+    from paper_1307_5824_gb300 import Reconstructor
+    from paper_1307_5824_gb300 import _lib as L
+    inp = workload(args.images, args.N, args.workload)
+    N, M = inp["N"], inp["M"]
+    dev = torch.device("cuda")
+    img = torch.from_numpy(inp["images"]).to(dev).to(torch.bfloat16)
+    R = torch.from_numpy(inp["R"].reshape(M, 9).copy()).to(dev)
+    g = torch.from_numpy(inp["group_id"]).to(dev)
+    sh = torch.from_numpy(inp["shifts"]).to(dev)
+    rec = Reconstructor(N, M, groups=inp["groups"], W=args.W, lam=1e-3, img_dtype=L.FIRM_IMG_BF16, fused=True)
+    rec.set_timing(True)
+    for form in ("separate", "separate", "fused", "fused"):
+        if form == "fused":
+            rec.kernel_backproject(img, sh, R, g)
+        else:
+            rec.kernel(R, g)
+            rec.backproject(img, sh, R, g)
+        torch.cuda.synchronize()
+        print(form, {k: round(v, 3) for k, v in rec.stage_times().items() if k not in ("cg", "cg_iters")})
+    rec.close()
 
 
 # ---------------------------------------------------------------------------
@@ -500,6 +577,8 @@ def main():
         return run_reference(args)
     if args.workload == "C4":
         return run_batched(args)
+    if args.spread_only:
+        return run_spread_only(args)
     import torch
     import torch.distributed as dist
 

@@ -442,7 +442,7 @@ typedef struct {
     float* x;               /* device, N^3 float32: the reconstructed volume */
 } firm_batch_item;
 
-enum { FIRM_BATCH_GRAPH = 1, FIRM_BATCH_PERSISTENT = 2 };
+enum { FIRM_BATCH_GRAPH = 1, FIRM_BATCH_PERSISTENT = 2, FIRM_BATCH_LEARNED = 4 };
 
 int firm_batch_workspace_size(int n_plans, size_t* bytes);
 /* plans: n_plans distinct plans (not destroyed while the batch lives).  n_streams in
@@ -453,6 +453,25 @@ int firm_batch_create(firm_batch_t* out, int n_plans, const firm_plan_t* plans, 
 /* Queues every reconstruction (items[i] for plans[i]) on the batch's stream and
  * returns without waiting.  iters in 0..20000; flags: FIRM_BATCH_*. */
 int firm_batch_run(firm_batch_t batch, const firm_batch_item* items, int iters, int flags);
+/* Every reconstruction solved to a relative residual (Section 3.3 with the stopping rule
+ * of firm_cg_solve): steps 1-3 as firm_batch_run (graph-captured with FIRM_BATCH_GRAPH,
+ * persistent spreading with FIRM_BATCH_PERSISTENT), then preconditioned CG from x0 = 0
+ * until ||r|| <= rel_tol ||A*b|| or max_iter, every plan on its own.  Preconditioner of
+ * plan i: with FIRM_BATCH_LEARNED the batch's network (firm_batch_set_network) maps the
+ * plans' density features (firm_pc_net_input), all plans in one forward pass, to their
+ * FIRM_PRECOND_TABLE tables; otherwise the plan's own mode (firm_set_precond; NONE,
+ * CIRCULANT or a TABLE set with firm_set_precond_table; BINNED needs the host per plan
+ * and gives FIRM_EINVAL).  The iterations run in chunks of 8 per plan (one CUDA graph
+ * per chunk with FIRM_BATCH_GRAPH); between chunks the host reads one count of the plans
+ * not yet stopped, so the call returns when every plan has stopped.  The volumes are in
+ * items[i].x; firm_batch_wait reports per plan FIRM_OK, FIRM_ENOTCONV (rel_tol not met
+ * at max_iter) or FIRM_EBREAKDOWN and the iterations.  Not in the paper (an execution
+ * form and an addition to its CG).  FIRM_ESTATE: FIRM_BATCH_LEARNED without a network. */
+int firm_batch_solve(firm_batch_t batch, const firm_batch_item* items, int max_iter, double rel_tol, int flags);
+/* The learned preconditioner's network for firm_batch_solve: params_bf16 (the BF16
+ * weights of firm_mlp_to_bf16) and params (FP32, for the biases), device memory the
+ * caller keeps alive; NULL, NULL removes it. */
+int firm_batch_set_network(firm_batch_t batch, const void* params_bf16, const float* params);
 /* Waits for the batch, then reports per plan the CG status (firm_status) and the
  * iterations run; also leaves each plan as after its own firm_kernel /
  * firm_backproject (lam_eff, Ker, K-hat and A*b readable).  Returns FIRM_OK when every

@@ -20,7 +20,7 @@ FIRM_IMG_F32, FIRM_IMG_BF16 = 0, 1
 FIRM_LAMBDA_RELATIVE, FIRM_LAMBDA_ABSOLUTE = 0, 1
 FIRM_OUT_KER, FIRM_OUT_KHAT, FIRM_OUT_RHS, FIRM_OUT_SAMPLES, FIRM_OUT_BIN_IDS, FIRM_OUT_BIN_WORK = 0, 1, 2, 3, 4, 5
 FIRM_PRECOND_NONE, FIRM_PRECOND_CIRCULANT, FIRM_PRECOND_BINNED, FIRM_PRECOND_TABLE = 0, 1, 2, 3
-FIRM_BATCH_GRAPH, FIRM_BATCH_PERSISTENT = 1, 2
+FIRM_BATCH_GRAPH, FIRM_BATCH_PERSISTENT, FIRM_BATCH_LEARNED = 1, 2, 4
 FIRM_FLAG_FP64_CG, FIRM_FLAG_FUSED = 1, 2
 
 EXPORTED = [
@@ -33,7 +33,8 @@ EXPORTED = [
     "firm_mlp_forward", "firm_mlp_to_bf16", "firm_mlp_forward_bf16", "firm_mlp_grad",
     "firm_mlp_adam", "firm_mlp_param_count", "firm_mlp_work_floats",
     "firm_bin", "firm_bin_info",
-    "firm_batch_workspace_size", "firm_batch_create", "firm_batch_run", "firm_batch_wait", "firm_batch_set_config",
+    "firm_batch_workspace_size", "firm_batch_create", "firm_batch_run", "firm_batch_solve", "firm_batch_set_network",
+    "firm_batch_wait", "firm_batch_set_config",
     "firm_batch_get_config", "firm_batch_tune", "firm_batch_launch_count", "firm_batch_destroy",
     "firm_destroy", "firm_strerror",
 ]
@@ -111,6 +112,8 @@ def lib() -> ctypes.CDLL:
     L.firm_batch_workspace_size.argtypes = [i, ctypes.POINTER(ctypes.c_size_t)]
     L.firm_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), i, vp, ctypes.c_size_t, vp]
     L.firm_batch_run.argtypes = [vp, ctypes.POINTER(firm_batch_item), i, i]
+    L.firm_batch_solve.argtypes = [vp, ctypes.POINTER(firm_batch_item), i, d, i]
+    L.firm_batch_set_network.argtypes = [vp, vp, vp]
     L.firm_batch_wait.argtypes = [vp, vp, vp]
     L.firm_batch_set_config.argtypes = [vp, i, i]
     L.firm_batch_get_config.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -378,6 +381,14 @@ def firm_batch_create(plans, n_streams: int, workspace, workspace_bytes: int, st
 
 def firm_batch_run(batch, items_arr, iters: int, flags: int):
     _check(lib().firm_batch_run(batch, items_arr, int(iters), int(flags)), "firm_batch_run")
+
+
+def firm_batch_solve(batch, items_arr, max_iter: int, rel_tol: float, flags: int):
+    _check(lib().firm_batch_solve(batch, items_arr, int(max_iter), float(rel_tol), int(flags)), "firm_batch_solve")
+
+
+def firm_batch_set_network(batch, params_bf16, params):
+    _check(lib().firm_batch_set_network(batch, _ptr(params_bf16), _ptr(params)), "firm_batch_set_network")
 
 
 def firm_batch_wait(batch, n: int, allow=()):

@@ -39,6 +39,22 @@ class BatchReconstructor:
         flags = (L.FIRM_BATCH_GRAPH if graph else 0) | (L.FIRM_BATCH_PERSISTENT if persistent else 0)
         L.firm_batch_run(self.batch, self._items, iters, flags)
 
+    def solve(self, max_iter: int, rel_tol: float, graph: bool = True, persistent: bool = True,
+              learned: bool = False):
+        """Every reconstruction to rel_tol (or max_iter) with its plan's preconditioner, or
+        with the batch's network (set_network) when learned; returns when all are done."""
+        flags = ((L.FIRM_BATCH_GRAPH if graph else 0) | (L.FIRM_BATCH_PERSISTENT if persistent else 0) |
+                 (L.FIRM_BATCH_LEARNED if learned else 0))
+        L.firm_batch_solve(self.batch, self._items, max_iter, rel_tol, flags)
+
+    def set_network(self, params: torch.Tensor):
+        """The learned preconditioner's network (FP32 parameters on the device) for
+        solve(learned=True); its BF16 copy is made here, on the batch's stream."""
+        self._net = params
+        self._net_bf16 = torch.empty(params.numel(), dtype=torch.bfloat16, device=params.device)
+        L.firm_mlp_to_bf16(params, self._net_bf16, self.stream.cuda_stream)
+        L.firm_batch_set_network(self.batch, self._net_bf16, self._net)
+
     def wait(self, allow=()):
         return L.firm_batch_wait(self.batch, len(self.recs), allow)
 

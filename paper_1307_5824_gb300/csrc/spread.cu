@@ -740,11 +740,21 @@ __global__ void k_batch_items(const SpreadArgs* __restrict__ desc, int n, int* _
 // spread_piece: the kernel channel's scale comes from the largest h^2 of the CTF table,
 // the A*b scale from the piece's own largest |h b|; PPR points per thread between folds.
 // ---------------------------------------------------------------------------
-struct FusedRound { static constexpr int PPR = 2; static constexpr int kScaleBits = 21; };
+// T threads per block (256; the three planes take 66 KB at W = 6, three blocks per SM:
+// 512-thread blocks, twice the warps per SM, measured 10% slower); with PPR points per
+// thread between folds a cell takes at most T * PPR taps, each at most 2^kScaleBits:
+// T * PPR * 2^kScaleBits <= 2^30.
+constexpr int kFusedThreads = 256;
+template <int T> struct FusedRound {
+    static constexpr int PPR = T >= 512 ? 1 : 2;
+    static constexpr int kScaleBits = 21;
+    static_assert(T * PPR <= 512, "fold bound");
+};
 
-template <int W>
+template <int W, int T>
 __device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const KbPoly& poly, const int4 wk, int* lev1,
                                                    float* lev2, float* s_red) {
+    constexpr int kWarps = T / 32;
     constexpr int BZ = kBrickZk;
     constexpr int RG = kBrick + W;
     constexpr int RG3 = RG * RG * (BZ + W);
@@ -755,11 +765,11 @@ __device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const Kb
     const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
     const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * BZ;
     const uint32_t s0 = (uint32_t)wk.y + threadIdx.x;
-    const int my_n = wk.z > (int)threadIdx.x ? (wk.z - (int)threadIdx.x + kSpreadThreads - 1) / kSpreadThreads : 0;
+    const int my_n = wk.z > (int)threadIdx.x ? (wk.z - (int)threadIdx.x + T - 1) / T : 0;
     // largest |h b| of the piece (the A*b scale)
     float wmax = 0.0f;
     for (int i = 0; i < my_n; ++i) {
-        const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
+        const uint32_t id = __ldg(&a.payload[s0 + T * i]);
         const float2 wv = __ldg(&a.samples[(size_t)(id >> kTBits) * a.nH + (id & ((1u << kTBits) - 1u))]);
         wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
     }
@@ -769,9 +779,9 @@ __device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const Kb
     __syncthreads();
     wmax = s_red[0];
 #pragma unroll
-    for (int i = 1; i < kSpreadWarps; ++i) wmax = fmaxf(wmax, s_red[i]);
-    constexpr int PPR = FusedRound::PPR, SB = FusedRound::kScaleBits;
-    const int rounds = (((wk.z + kSpreadThreads - 1) / kSpreadThreads) + PPR - 1) / PPR;
+    for (int i = 1; i < kWarps; ++i) wmax = fmaxf(wmax, s_red[i]);
+    constexpr int PPR = FusedRound<T>::PPR, SB = FusedRound<T>::kScaleBits;
+    const int rounds = (((wk.z + T - 1) / T) + PPR - 1) / PPR;
     int ek = 0, eb = 0;
     if (a.wmax_fixed > 0.0f) frexpf(a.wmax_fixed, &ek);
     if (wmax > 0.0f) frexpf(wmax, &eb);
@@ -782,7 +792,7 @@ __device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const Kb
         for (int q = 0; q < PPR; ++q) {
             const int i = PPR * r + q;
             if (i >= my_n) continue;
-            const uint32_t pos = s0 + kSpreadThreads * i;
+            const uint32_t pos = s0 + T * i;
             const uint32_t id = __ldg(&a.payload[pos]);
             const int m = (int)(id >> kTBits);
             const int t = (int)(id & ((1u << kTBits) - 1u));
@@ -854,13 +864,13 @@ __device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const Kb
 }
 
 template <int W>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread_fused(const SpreadArgs a) {
+__global__ void __launch_bounds__(kFusedThreads) k_spread_fused(const SpreadArgs a) {
     constexpr int R3 = (kBrick + W) * (kBrick + W) * (kBrickZk + W);
     extern __shared__ int sm_i[];
     int* lev1 = sm_i;                                          // 3 * R3 int32
     float* lev2 = reinterpret_cast<float*>(sm_i + 3 * R3);     // 3 * R3 float
     __shared__ int s_item;
-    __shared__ float s_red[kSpreadWarps];
+    __shared__ float s_red[kFusedThreads / 32];
     for (int i = threadIdx.x; i < 6 * R3; i += blockDim.x) sm_i[i] = 0;
     const int n_work = a.counters[0];
     for (;;) {
@@ -869,7 +879,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_fused(const SpreadArg
         __syncthreads();
         const int item = s_item;
         if (item >= n_work) break;
-        spread_piece_fused<W>(a, a.poly, a.work[item], lev1, lev2, s_red);
+        spread_piece_fused<W, kFusedThreads>(a, a.poly, a.work[item], lev1, lev2, s_red);
     }
 }
 
@@ -880,10 +890,10 @@ static cudaError_t spread_fused_w(Plan& P, const SpreadArgs& a) {
     cudaError_t e = cudaFuncSetAttribute(k_spread_fused<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_fused<W>, kSpreadThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_fused<W>, kFusedThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    k_spread_fused<W><<<P.num_sms * per_sm, kSpreadThreads, smem, P.stream>>>(a);
+    k_spread_fused<W><<<P.num_sms * per_sm, kFusedThreads, smem, P.stream>>>(a);
     P.launches += 1;
     return cudaGetLastError();
 }

@@ -148,3 +148,111 @@ def test_batch_rejects_bad_arguments(F):
     B.close()
     for r in recs:
         r.close()
+
+
+def _true_res(L, rec, x):
+    """||A*b - (A*A + lam_eff) x|| / ||A*b|| of a plan's volume (one Toeplitz apply)."""
+    y = torch.empty_like(x)
+    b = torch.empty_like(x)
+    rec.toeplitz_apply(x, y)
+    rec.copy_out(L.FIRM_OUT_RHS, b)
+    torch.cuda.synchronize()
+    bn = b.double().cpu().numpy()
+    return float(np.linalg.norm(bn - y.double().cpu().numpy()) / np.linalg.norm(bn))
+
+
+def _single_solve(F, p, max_iter, rel_tol, mode=None, infer=None):
+    """The single-plan path to a tolerance: firm_cg_solve with the plan's preconditioner."""
+    N, M = p["N"], p["M"]
+    rec = F.Reconstructor(N, max(M, 1), groups=p["groups"], W=6, lam=1e-3)
+    it = _dev_item(p, None)
+    rec.kernel(it["R"], it["group"], M=M)
+    rec.backproject(it["images"], it["shifts"], it["R"], it["group"], M=M)
+    if infer is not None:
+        infer.apply(rec)
+    elif mode is not None:
+        rec.set_precond(mode)
+    x = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    st, n = rec.cg_solve(x, max_iter, rel_tol=rel_tol, allow=(F._lib.FIRM_ENOTCONV,))
+    torch.cuda.synchronize()
+    out = x.cpu().numpy()
+    rec.close()
+    return out, n
+
+
+def test_batch_solve_to_tolerance_with_each_preconditioner(F, problems):
+    """firm_batch_solve: every plan of the batch to rel-res 1e-3 with plain CG, with its own
+    circulant preconditioner and with the batch's learned network (one forward pass for
+    all plans), in chunked CG with and without a CUDA graph.  Every volume meets the
+    tolerance (its true residual, recomputed) and needs the iterations the single-plan
+    firm_cg_solve needs, within a few (a long CG run's stopping iteration moves with the
+    last bits of Ker, whose FP64 atomics add in a different order run to run); the
+    network needs fewer iterations in total than plain CG; a circulant-preconditioned
+    member after 8 iterations matches the oracle's PCG (Section 3.3's CG with a
+    preconditioner)."""
+    from paper_1307_5824_gb300 import learned
+    L = F._lib
+    tol = 1e-3
+    X, T = learned.generate(64, N=32, seed=61, m_range=(60, 300))
+    net, _ = learned.train(X, T, steps=800, batch=16, lr=1e-3, log_every=200)
+    infer = learned.DeviceInference(net)
+    recs = [F.Reconstructor(p["N"], max(p["M"], 1), groups=p["groups"], W=6, lam=1e-3) for p in problems]
+    xs = [torch.zeros((p["N"],) * 3, dtype=torch.float32, device="cuda") for p in problems]
+    items = [_dev_item(p, x) for p, x in zip(problems, xs)]
+    B = F.BatchReconstructor(recs, n_streams=4)
+    B.set_items(items)
+    B.set_network(net)
+    totals = {}
+    for name, mode in (("plain", L.FIRM_PRECOND_NONE), ("circulant", L.FIRM_PRECOND_CIRCULANT),
+                       ("learned", None)):
+        for r in recs:
+            r.set_precond(mode if mode is not None else L.FIRM_PRECOND_NONE)
+        for graph in (False, True):
+            for x in xs:
+                x.zero_()
+            B.solve(1000, tol, graph=graph, learned=mode is None)
+            st, sts, its = B.wait(allow=(L.FIRM_ENOTCONV,))
+            assert (sts == 0).all() or mode is None, (name, sts)
+            for k, (p, x) in enumerate(zip(problems, xs)):
+                if p["M"] == 0:
+                    assert float(x.abs().max()) == 0.0
+                    continue
+                ref, n_ref = _single_solve(F, p, 1000, tol, mode=mode, infer=infer if mode is None else None)
+                tr = _true_res(L, recs[k], x)
+                e = rel(x.cpu().numpy(), ref)
+                print(name, graph, k, "iterations", int(its[k]), n_ref, "true res %.2e" % tr, "vs single %.1e" % e)
+                assert abs(int(its[k]) - n_ref) <= max(3, 0.05 * n_ref), (name, graph, k, int(its[k]), n_ref)
+                if sts[k] == 0:
+                    assert tr <= 2 * tol and e <= 20 * tol, (name, graph, k, tr, e)
+                else:                                   # the single-plan solve stops at max_iter too
+                    assert n_ref == 1000 and e <= 1e-2, (name, graph, k, n_ref, e)
+        totals[name] = int(its.sum())
+    print("batched iterations to rel-res 1e-3:", totals)
+    assert totals["learned"] < totals["plain"] and totals["circulant"] < totals["plain"]
+    # a preconditioned member after a fixed count against the oracle's PCG
+    for r in recs:
+        r.set_precond(L.FIRM_PRECOND_CIRCULANT)
+    B.solve(8, 0.0)
+    B.wait()
+    p = problems[2]                                      # N = 32, 150 images, 4 groups
+    N = p["N"]
+    K = O.disc(N)
+    h = O.ctf_weights(N, K, p["groups"], p["gid"])
+    Ker = O.kernel(p["R"], h, K, N).real
+    rhs = O.backproject(p["images"].astype(np.float64), p["shifts"], p["R"], h, K)
+    lam = O.lambda_eff(1e-3, 0, Ker[N, N, N])
+    Kh = O.khat(Ker).real
+    Pc = O.circulant_preconditioner(O.wrapped_spectrum(Ker), lam)
+    xo, _, _ = O.cg(lambda v: O.toeplitz_apply(Kh, v, lam).real, rhs, 8, precond=Pc)
+    e = rel(xs[2].cpu().numpy(), xo)
+    print(f"batched PCG member vs oracle after 8 iterations: {e:.2e}")
+    assert e <= 1e-4
+    # learned without a network is refused
+    B.set_network(net)
+    L.firm_batch_set_network(B.batch, None, None)
+    with pytest.raises(F.FirmError) as ex:
+        B.solve(10, tol, learned=True)
+    assert ex.value.code == L.FIRM_ESTATE
+    B.close()
+    for r in recs:
+        r.close()

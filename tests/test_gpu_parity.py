@@ -407,3 +407,50 @@ def test_preconditioned_cg_matches_oracle(F):
     assert st == 0 and it_pc < it_plain
     true_res = np.linalg.norm(op(x.cpu().numpy().astype(np.float64)) - rhs) / np.linalg.norm(rhs)
     assert true_res <= 3e-4
+
+
+@pytest.mark.parametrize("N,M", [(48, 120), (80, 150)])
+def test_preconditioned_cg_matches_oracle_at_uneven_sizes(F, N, M):
+    """PCG at the batched workload's non-power-of-two sizes (N = 48, 80: FFT lengths 48, 80,
+    96, 160): the circulant preconditioner and a table preconditioner (exp(t_b) / Ker(0)
+    per shell x cone bin, Section 3.3's CG preconditioned) after 8 iterations against
+    the oracle's PCG.  Ker and A*b of the oracle come from its gridding mode (W = 12).
+    Gate 2e-4: these lambda = 1e-3 PCG iterates carry the W = 7 window error of Ker and A*b
+    (~1e-6) amplified over the 8 steps (1.2e-4 measured at N = 80); the table varies
+    slowly across bins, since a frequency on a bin edge may fall on either side in FP32
+    and FP64."""
+    from oracle import gridding as Gr
+    from oracle import lpre as LP
+    inp = _inputs("C2", N, M)
+    K = O.disc(N)
+    rec = F.Reconstructor(N, M, groups=inp["groups"], W=7, lam=1e-3)
+    R = _dev(inp["R"].reshape(M, 9))
+    g = _dev(inp["group_id"])
+    rec.kernel(R, g)
+    rec.backproject(_dev(inp["images"]), _dev(inp["shifts"]), R, g)
+    Ker = Gr.kernel_gridded(inp["R"], inp["groups"], inp["group_id"], K, N, W=12).real
+    rhs = Gr.backproject_gridded(inp["images"], inp["shifts"], inp["R"], inp["groups"], inp["group_id"], K, W=12)
+    lam = O.lambda_eff(1e-3, 0, Ker[N, N, N])
+    Kh = O.khat(Ker).real
+    op = lambda v: O.toeplitz_apply(Kh, v, lam).real
+    x = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    # circulant
+    rec.set_precond(F._lib.FIRM_PRECOND_CIRCULANT)
+    rec.cg_solve(x, 8)
+    xo, _, _ = O.cg(op, rhs, 8, precond=O.circulant_preconditioner(O.wrapped_spectrum(Ker), lam))
+    e_c = rel(x.cpu().numpy(), xo)
+    # a table: smooth in the shell index, varying with the cone
+    s_idx = np.arange(64)[:, None]
+    c_idx = np.arange(16)[None, :]
+    table = (-0.01 * s_idx + 0.02 * np.cos(c_idx / 3.0)).astype(np.float32).ravel()
+    rec.set_precond_table(table)
+    rec.cg_solve(x, 8)
+    a = rec.pc_axis().astype(np.float64)
+    a /= np.linalg.norm(a)
+    d = LP.table_diagonal(table.astype(np.float64), N, Ker[N, N, N], a)
+    pc = lambda r: np.fft.ifftn(d * np.fft.fftn(r)).real
+    xt, _, _ = O.cg(op, rhs, 8, precond=pc)
+    e_t = rel(x.cpu().numpy(), xt)
+    print(f"PCG N={N}: circulant {e_c:.2e} table {e_t:.2e}")
+    assert e_c <= 2e-4 and e_t <= 2e-4
+    rec.close()
