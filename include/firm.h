@@ -13,7 +13,9 @@
  * Conventions (shared by every entry point):
  *   - A volume is N^3 float32, row-major [i3][i2][i1] (i1 = x fastest), voxel index
  *     i_j <-> centred coordinate n_j = i_j - N/2 (Section 3.1).
- *   - Images are M x N x N, [m][i2][i1], float32 or bfloat16 (firm_params.img_dtype).
+ *   - Images are M x N x N, [m][i2][i1], float32 or bfloat16 (firm_params.img_dtype),
+ *     starting at a 16-byte aligned address (each image is moved into shared memory by
+ *     one bulk copy); a misaligned image array is rejected with FIRM_EINVAL.
  *   - R is M x 9 float64, each rotation row-major.  The slice of image m samples
  *     the points xi = R_m^T (2 pi k1 / N, 2 pi k2 / N, 0) for |k| <= N/2
  *     (eq. forward-projector, eq. truncation: the symmetric disc).
@@ -63,7 +65,8 @@ typedef enum {
     FIRM_ETIMEOUT = 6,    /* a bounded device wait gave up (never expected) */
     FIRM_ESTATE = 7,      /* call order: e.g. firm_cg_solve before firm_kernel */
     FIRM_EINTERNAL = 8    /* an internal invariant failed on the device (a binned point
-                           * outside its brick; never expected).  Device kernels record it
+                           * outside its brick, or a bounded wait for an asynchronous copy
+                           * that gave up; never expected).  Device kernels record it
                            * in the plan; it is reported, and cleared, by the next call that
                            * waits for the stream (a host output, firm_cg_solve,
                            * firm_lambda_eff, firm_pc_axis), not by the call that queued it. */

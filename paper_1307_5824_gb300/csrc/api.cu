@@ -626,9 +626,11 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     return put_out_checked(P, khat_out, w.khat, sizeof(float) * 2 * P.N * 2 * P.N * (P.N + 1));
 }
 
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 int firm_backproject(firm_plan_t plan, int M, const void* images, const double* shifts, const double* R,
                      const int32_t* group, float* rhs_out) {
-    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !images))) return FIRM_EINVAL;
+    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !images || !aligned16(images)))) return FIRM_EINVAL;
     Plan& P = plan->P;
     Workspace& w = P.ws;
     cudaError_t e = cudaSuccess;
@@ -676,7 +678,7 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
 
 int firm_kernel_backproject(firm_plan_t plan, int M, const void* images, const double* shifts, const double* R,
                             const int32_t* group, float* khat_out, float* rhs_out) {
-    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !images))) return FIRM_EINVAL;
+    if (!plan || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !images || !aligned16(images)))) return FIRM_EINVAL;
     Plan& P = plan->P;
     if (!(P.p.flags & FIRM_FLAG_FUSED)) return FIRM_EINVAL;
     Workspace& w = P.ws;
@@ -781,7 +783,8 @@ int firm_stage_images(firm_plan_t plan, int M, const void* images, void* staging
     Plan& P = plan->P;
     const size_t esz = P.p.img_dtype == FIRM_IMG_BF16 ? 2 : 4;
     const size_t bytes = (size_t)M * P.N * P.N * esz;
-    if (M > 0 && (is_device(images) || !is_device(staging) || staging_bytes < bytes)) return FIRM_EINVAL;
+    if (M > 0 && (is_device(images) || !is_device(staging) || staging_bytes < bytes || !aligned16(staging)))
+        return FIRM_EINVAL;
     if (!P.copy_stream) {
         FIRM_CK(cudaStreamCreateWithFlags(&P.copy_stream, cudaStreamNonBlocking));
         FIRM_CK(cudaEventCreateWithFlags(&P.ev_inputs, cudaEventDisableTiming));
@@ -830,7 +833,8 @@ int firm_forward(firm_plan_t plan, int M, const float* V, const double* R, const
 
 int firm_data_residual(firm_plan_t plan, int M, const float* V, const void* images, const double* shifts,
                        const double* R, const int32_t* group, double* out2) {
-    if (!plan || !out2 || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !V || !images))) return FIRM_EINVAL;
+    if (!plan || !out2 || M < 0 || M > plan->P.p.M || (M > 0 && (!R || !V || !images || !aligned16(images))))
+        return FIRM_EINVAL;
     Plan& P = plan->P;
     Workspace& w = P.ws;
     if (M == 0) {
@@ -1220,7 +1224,7 @@ const char* firm_strerror(int code) {
         case FIRM_EBREAKDOWN: return "CG breakdown";
         case FIRM_ETIMEOUT: return "device wait timed out";
         case FIRM_ESTATE: return "call order (kernel or right-hand side missing)";
-        case FIRM_EINTERNAL: return "internal invariant failed on the device (a binned point outside its brick)";
+        case FIRM_EINTERNAL: return "internal invariant failed on the device (a binned point outside its brick or a copy wait that gave up)";
         default: return "unknown status";
     }
 }

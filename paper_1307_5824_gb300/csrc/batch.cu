@@ -409,6 +409,7 @@ int check_items(const firm_batch_s& b, const firm_batch_item* items) {
         const Plan& P = b.plans[i]->P;
         if (it.M < 0 || it.M > P.p.M || !it.x || !dev_ptr(it.x)) return FIRM_EINVAL;
         if (it.M > 0 && (!dev_ptr(it.R) || !dev_ptr(it.images))) return FIRM_EINVAL;
+        if (it.M > 0 && (reinterpret_cast<uintptr_t>(it.images) & 15)) return FIRM_EINVAL;   // bulk-copied
         if (it.group && !dev_ptr(it.group)) return FIRM_EINVAL;
         if (it.shifts && !dev_ptr(it.shifts)) return FIRM_EINVAL;
     }

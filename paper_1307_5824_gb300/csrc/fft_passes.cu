@@ -26,6 +26,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "bulk.cuh"
 #include "dw.cuh"
 #include "fft.cuh"
 #include "firm_internal.h"
@@ -419,12 +420,14 @@ struct ImgArgs {
     const void* images; const double* shifts; const int32_t* gid; const int32_t* htab;
     const float* h1; float2* samples; const float2* tw; int nH, n_ctf;
     int plain;              // 1: b itself (no h, k = 0 not halved), for the data residual
+    int* err;               // device failure flag (bit 2: the image copy did not land in time)
 };
 
-template <int N, class T>
-__device__ __forceinline__ float img_val(const void* p, size_t i) {
-    if constexpr (sizeof(T) == 2) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[i]);
-    else return __ldg(reinterpret_cast<const float*>(p) + i);
+// A pixel of the image staged in shared memory (float32 or bfloat16 bits).
+template <class T>
+__device__ __forceinline__ float img_val(const T* p, int i) {
+    if constexpr (sizeof(T) == 2) return __bfloat162float(__ushort_as_bfloat16(p[i]));
+    else return p[i];
 }
 
 template <int N> __host__ __device__ constexpr int img_rows() { return kThreads / Split<N>::L2; }
@@ -439,20 +442,39 @@ template <int N> __host__ __device__ constexpr int img_smem_elems() {
 template <int N, class T>
 __global__ void __launch_bounds__(kThreads) k_image_dft(const ImgArgs a) {
     extern __shared__ float2 sm2[];
+    __shared__ __align__(8) unsigned long long s_bar;
     constexpr int H1 = N / 2 + 1;
     float2* S1 = sm2;
     float2* scr = sm2 + N * H1;
     const int m = blockIdx.x;
     const size_t img0 = (size_t)m * N * N;
     constexpr int ROWS = img_rows<N>();
+    // The image arrives with one bulk copy (the tensor memory accelerator) into the tail
+    // of S1: the row transforms write S1 rows 2j, 2j+1 only after reading image rows 2j,
+    // 2j+1 (each batch loads all its inputs before it stores), and with the image ending
+    // where S1 ends, the rows written so far never reach the rows still to be read
+    // (written bytes 16 H1 p <= unread offset S1 - img + 2 N sizeof(T) p for every p <= N/2).
+    constexpr uint32_t kImgBytes = (uint32_t)(N * N * sizeof(T));
+    constexpr uint32_t kS1Bytes = (uint32_t)(sizeof(float2) * N * H1);
+    static_assert(kImgBytes <= kS1Bytes && (kS1Bytes - kImgBytes) % 16 == 0 && kImgBytes % 16 == 0, "staging");
+    const T* img = reinterpret_cast<const T*>(reinterpret_cast<const unsigned char*>(S1) + (kS1Bytes - kImgBytes));
+    if (threadIdx.x == 0) mbar_init(&s_bar);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        bulk_g2s(const_cast<T*>(img), reinterpret_cast<const T*>(a.images) + img0, kImgBytes, &s_bar);
+    if (!mbar_wait(&s_bar, 0)) {
+        if (threadIdx.x == 0) atomicOr(a.err, 4);
+        mbar_wait(&s_bar, 0);                      // the copy in flight, then leave
+        return;
+    }
     // rows 2j and 2j+1 (real) transformed together as z = x_2j + i x_2j+1: Z[k] for
     // k <= N/2 goes to row 2j's slots, Z[k] for k > N/2 to row 2j+1's (slot k - N/2 - 1)
     constexpr int NP = N / 2;
     for (int l0 = 0; l0 < NP; l0 += ROWS) {
         const int nl = min(ROWS, NP - l0);
         auto ld = [&](int line, int n) {
-            const size_t i = img0 + (size_t)(2 * (l0 + line)) * N + n;
-            return make_float2(img_val<N, T>(a.images, i), img_val<N, T>(a.images, i + N));
+            const int i = (2 * (l0 + line)) * N + n;
+            return make_float2(img_val<T>(img, i), img_val<T>(img, i + N));
         };
         auto st = [&](int line, int k, float2 v) {
             const int j = l0 + line;
@@ -530,7 +552,11 @@ static cudaError_t image_dft_n(Plan& P, int M, const ImgArgs& a) {
 cudaError_t launch_image_dft(Plan& P, int M, const void* images, const double* shifts, const int32_t* gid,
                              bool plain) {
     if (M <= 0) return cudaSuccess;
-    ImgArgs a{images, shifts, gid, P.ws.htab, P.ws.h1, P.ws.samples, P.ws.tw_n, P.nH, P.n_ctf, plain ? 1 : 0};
+    // each image is staged by a bulk copy, which needs a 16-byte aligned source (every
+    // entry point checks this before it queues any work)
+    if (reinterpret_cast<uintptr_t>(images) & 15) return cudaErrorInvalidValue;
+    ImgArgs a{images, shifts, gid, P.ws.htab, P.ws.h1, P.ws.samples, P.ws.tw_n, P.nH, P.n_ctf, plain ? 1 : 0,
+              P.ws.counters + 2};
     const bool bf = P.p.img_dtype == FIRM_IMG_BF16;
     switch (P.N) {
         case 16: return bf ? image_dft_n<16, uint16_t>(P, M, a) : image_dft_n<16, float>(P, M, a);

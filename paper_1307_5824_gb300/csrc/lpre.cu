@@ -273,65 +273,148 @@ constexpr size_t kOffW1 = 0, kOffB1 = kOffW1 + (size_t)kW1 * kW0, kOffW2 = kOffB
 // C[M x N] = op(A) op(B) (+ bias[N]) (ReLU), op by leading-dimension flags.
 //   TA = false: A is M x K row-major; true: A is K x M row-major (use A^T).
 //   TB = false: B is K x N row-major; true: B is N x K row-major (use B^T).
-// 64 x 64 output tile per block, 16 x 16 threads, 4 x 4 per thread, K step 16.
+// On the tensor cores (mma.sync): a 64 x 64 output tile per block of
+// four warps, each warp 32 x 32 (2 x 4 tiles of 16 x 8), K in steps of 16 staged in
+// shared memory in a fixed [row][k] layout whatever the operands' transposition.
+//   BF16 weights (inference): both operands as bf16 (activations rounded), m16n8k16,
+//     FP32 accumulation.
+//   FP32 (training and the FP32 forward pass): three TF32 products per step with each
+//     operand split as x = hi + lo, hi = tf32(x), lo = tf32(x - hi) (hi*hi + hi*lo +
+//     lo*hi, the small terms first), m16n8k8, FP32 accumulation: FP32-level accuracy.
+constexpr int kTcTile = 64, kTcK = 16, kTcPad = 4;
+
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 template <bool TA, bool TB, class WT>
-__global__ void __launch_bounds__(256) k_gemm(const float* __restrict__ A, const WT* __restrict__ B, float* __restrict__ C,
-                                              int M, int N, int K, const float* __restrict__ bias, int relu,
-                                              int accumulate) {
-    __shared__ float As[16][64 + 1];
-    __shared__ float Bs[16][64 + 1];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
-            const int kk = i / 64, mm = i % 64;
+__global__ void __launch_bounds__(128) k_gemm_tc(const float* __restrict__ A, const WT* __restrict__ B,
+                                                 float* __restrict__ C, int M, int N, int K,
+                                                 const float* __restrict__ bias, int relu, int accumulate) {
+    constexpr bool kBf16 = sizeof(WT) == 2;
+    __shared__ float As[kTcTile][kTcK + kTcPad];     // [m][k]
+    __shared__ float Bs[kTcTile][kTcK + kTcPad];     // [n][k]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * kTcTile, n0 = blockIdx.x * kTcTile;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += kTcK) {
+        for (int i = threadIdx.x; i < kTcTile * kTcK; i += blockDim.x) {
+            // A: consecutive threads along the operand's contiguous axis
+            const int mm = TA ? i % kTcTile : i / kTcK, kk = TA ? i / kTcTile : i % kTcK;
             const int gm = m0 + mm, gk = k0 + kk;
             float va = 0.0f;
             if (gm < M && gk < K) va = TA ? A[(size_t)gk * M + gm] : A[(size_t)gm * K + gk];
-            As[kk][mm] = va;
-            const int gn = n0 + mm;
+            As[mm][kk] = va;
+            const int nn = TB ? i / kTcK : i % kTcTile, kb = TB ? i % kTcK : i / kTcTile;
+            const int gn = n0 + nn, gkb = k0 + kb;
             float vb = 0.0f;
-            if (gn < N && gk < K) {
-                if constexpr (sizeof(WT) == 2) vb = __bfloat162float(TB ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn]);
-                else vb = TB ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn];
+            if (gn < N && gkb < K) {
+                if constexpr (kBf16) vb = __bfloat162float(TB ? B[(size_t)gn * K + gkb] : B[(size_t)gkb * N + gn]);
+                else vb = TB ? B[(size_t)gn * K + gkb] : B[(size_t)gkb * N + gn];
             }
-            Bs[kk][mm] = vb;
+            Bs[nn][kb] = vb;
         }
         __syncthreads();
+        if constexpr (kBf16) {
+            uint32_t af[2][4], bfr[4][2];
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + 16 * i + g;
+                af[i][0] = bf16x2(As[r][2 * t], As[r][2 * t + 1]);
+                af[i][1] = bf16x2(As[r + 8][2 * t], As[r + 8][2 * t + 1]);
+                af[i][2] = bf16x2(As[r][2 * t + 8], As[r][2 * t + 9]);
+                af[i][3] = bf16x2(As[r + 8][2 * t + 8], As[r + 8][2 * t + 9]);
+            }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int j = 0; j < 4; ++j) {
+                const int n = wn + 8 * j + g;
+                bfr[j][0] = bf16x2(Bs[n][2 * t], Bs[n][2 * t + 1]);
+                bfr[j][1] = bf16x2(Bs[n][2 * t + 8], Bs[n][2 * t + 9]);
+            }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+            for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+        } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            for (int ks = 0; ks < kTcK; ks += 8) {
+                uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int r = wm + 16 * i + g;
+                    const float v[4] = {As[r][ks + t], As[r + 8][ks + t], As[r][ks + t + 4], As[r + 8][ks + t + 4]};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        ah[i][q] = tf32_of(v[q]);
+                        al[i][q] = tf32_of(v[q] - __uint_as_float(ah[i][q]));
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int n = wn + 8 * j + g;
+                    const float v[2] = {Bs[n][ks + t], Bs[n][ks + t + 4]};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        bh[j][q] = tf32_of(v[q]);
+                        bl[j][q] = tf32_of(v[q] - __uint_as_float(bh[j][q]));
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        mma_tf32(acc[i][j], al[i], bh[j]);
+                        mma_tf32(acc[i][j], ah[i], bl[j]);
+                        mma_tf32(acc[i][j], ah[i], bh[j]);
+                    }
+            }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
-            if (gm >= M || gn >= N) continue;
-            float v = acc[i][j];
-            if (bias) v += bias[gn];
-            if (relu) v = fmaxf(v, 0.0f);
-            float* c = &C[(size_t)gm * N + gn];
-            *c = accumulate ? *c + v : v;
-        }
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int gm = m0 + wm + 16 * i + g + (q >= 2 ? 8 : 0);
+                const int gn = n0 + wn + 8 * j + 2 * t + (q & 1);
+                if (gm >= M || gn >= N) continue;
+                float v = acc[i][j][q];
+                if (bias) v += bias[gn];
+                if (relu) v = fmaxf(v, 0.0f);
+                float* c = &C[(size_t)gm * N + gn];
+                *c = accumulate ? *c + v : v;
+            }
 }
 
 template <bool TA, bool TB, class WT>
 static void gemm(cudaStream_t s, const float* A, const WT* B, float* C, int M, int N, int K, const float* bias, bool relu,
                  bool acc = false) {
-    const dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<TA, TB, WT><<<grid, 256, 0, s>>>(A, B, C, M, N, K, bias, relu ? 1 : 0, acc ? 1 : 0);
+    const dim3 grid((N + kTcTile - 1) / kTcTile, (M + kTcTile - 1) / kTcTile);
+    k_gemm_tc<TA, TB, WT><<<grid, 128, 0, s>>>(A, B, C, M, N, K, bias, relu ? 1 : 0, acc ? 1 : 0);
 }
 
 // gy = 2 (y - t) / n, loss partials

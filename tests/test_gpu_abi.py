@@ -201,3 +201,26 @@ def test_image_shards_loaded_into_a_plan_match_the_whole_set(F):
     assert e.value.code == L.FIRM_EINVAL
     whole.close()
     loaded.close()
+
+
+def test_misaligned_images_are_refused(F):
+    """Each image is moved into shared memory by one bulk copy, which needs a 16-byte
+    aligned source: an image array starting 8 bytes into a buffer is refused with
+    FIRM_EINVAL before any GPU work (and an aligned one in the same buffer is taken)."""
+    L = F._lib
+    N, M = 16, 4
+    inp = synth.config_inputs("C2", M=M, N=N)
+    rec = F.Reconstructor(N, M, groups=inp["groups"], W=6)
+    R, g, sh = _dev(inp["R"].reshape(M, 9)), _dev(inp["group_id"]), _dev(inp["shifts"])
+    raw = torch.zeros(M * N * N + 4, dtype=torch.float32, device="cuda")
+    bad = raw[2:2 + M * N * N]                           # 8 bytes past a 256-byte boundary
+    with pytest.raises(L.FirmError) as e:
+        rec.backproject(bad, sh, R, g)
+    assert e.value.code == L.FIRM_EINVAL
+    good = raw[4:4 + M * N * N]                          # 16 bytes past it
+    good.copy_(torch.from_numpy(inp["images"].reshape(-1)).cuda())
+    rhs = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    rec.backproject(good, sh, R, g, rhs_out=rhs)
+    torch.cuda.synchronize()
+    assert torch.isfinite(rhs).all()
+    rec.close()
