@@ -170,6 +170,7 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.count = c.take<uint32_t>(nb3);
     w.cursor = c.take<uint32_t>(nb3);
     w.work = c.take<int4>(max_work);
+    w.scan_part = c.take<unsigned long long>(2 * (nb3 / kScanSpan + 1));
     w.item_part = c.take<double>(2 * max_work);
     w.counters = c.take<int>(8);
     // FP64 fine grid: Ker (4N^3 real) or A*b (2N^3 complex); the fused form holds both

@@ -22,6 +22,7 @@ constexpr int kMaxBatch = 1024;       // most plans one batch holds
 constexpr int kTBits = 13;            // point id = m << kTBits | t (t < 8192)
 constexpr int kMaxHist = 20001;       // residual history capacity (iterations + 1)
 constexpr int kRedSlots = 4096;       // per-block partial sums of a reduction
+constexpr int kScanSpan = 1024;       // bricks per block of the brick scan
 
 // Window polynomials: tap l of a point with fractional tap offset u in [0,1) has
 // weight phi(u + l - W/2) = sum_j c[l][j] z^j, z = 2u - 1 (Horner in z).
@@ -85,6 +86,7 @@ struct Workspace {
     float2* samples_b = nullptr;    // A*b weights in scatter order (written by the scatter pass)
     uint16_t* perm = nullptr;       // per payload position: index in scatter order within its piece
     int4* work = nullptr;           // (brick, start, count, -)
+    unsigned long long* scan_part = nullptr;   // brick scan: per-block (points, items) totals
     double* item_part = nullptr;    // per work item: two FP64 partial sums (data residual)
     int* counters = nullptr;        // [0] work items, [1] work cursor, [2] error flag
     double* grid = nullptr;         // fine grid, FP64 (real for Ker, complex for A*b)

@@ -256,63 +256,120 @@ __global__ void __launch_bounds__(256) k_bin_scatter2d(BinArgs a, int M, int hN,
     }
 }
 
-// Single-block scan over bricks: cursor = exclusive prefix of count; work items
-// (brick, start, length) of at most `chunk` points (chunk <= kChunk).
-__global__ void __launch_bounds__(1024) k_scan_work(const uint32_t* __restrict__ count, uint32_t* __restrict__ cursor,
-                                                    int nbricks, int4* __restrict__ work, int* __restrict__ counters,
-                                                    int max_work, int chunk) {
-    __shared__ unsigned long long s_pts[32];
-    __shared__ int s_items[32];
-    const int T = blockDim.x, tid = threadIdx.x;
-    const int per = ((nbricks + T - 1) / T + 3) & ~3;
-    const int b0 = min(nbricks, tid * per), b1 = min(nbricks, b0 + per);
-    unsigned long long pts = 0;
-    int items = 0;
-    for (int b = b0; b < b1; b += 4) {   // nbricks and per are multiples of 4
-        const uint4 c4 = *reinterpret_cast<const uint4*>(count + b);
-        pts += (unsigned long long)c4.x + c4.y + c4.z + c4.w;
-        items += (int)((c4.x + chunk - 1) / chunk) + (int)((c4.y + chunk - 1) / chunk) +
-                 (int)((c4.z + chunk - 1) / chunk) + (int)((c4.w + chunk - 1) / chunk);
-    }
-    const int lane = tid & 31, wid = tid >> 5;
-    unsigned long long ip = pts;
-    int ii = items;
+// Scan over bricks: cursor = exclusive prefix of count; work items (brick, start,
+// length) of at most `chunk` points (chunk <= kChunk), numbered in brick order.  Three
+// launches: per-block totals of points and items over kScanSpan bricks, an exclusive
+// scan of those totals (one block), and the per-block scan that writes cursors and
+// items from its block's offsets.  nbricks is a multiple of 4.
+constexpr int kScanThreads = kScanSpan / 4;     // one uint4 of counts per thread
+struct ScanPart {
+    unsigned long long pts;
+    long long items;
+};
+
+// Block-wide inclusive scan of (pts, items); returns the block totals in thread 0's view
+// through s_tot.
+__device__ __forceinline__ void block_scan2(unsigned long long& ip, long long& ii, ScanPart* s_w, ScanPart* s_tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long vp = __shfl_up_sync(0xffffffffu, ip, o);
-        int vi = __shfl_up_sync(0xffffffffu, ii, o);
+        const unsigned long long vp = __shfl_up_sync(0xffffffffu, ip, o);
+        const long long vi = __shfl_up_sync(0xffffffffu, ii, o);
         if (lane >= o) { ip += vp; ii += vi; }
     }
-    if (lane == 31) { s_pts[wid] = ip; s_items[wid] = ii; }
+    if (lane == 31) s_w[wid] = ScanPart{ip, ii};
     __syncthreads();
     if (wid == 0) {
-        const int nw = T / 32;
-        unsigned long long vp = lane < nw ? s_pts[lane] : 0ull;
-        int vi = lane < nw ? s_items[lane] : 0;
+        const int nw = blockDim.x / 32;
+        unsigned long long vp = lane < nw ? s_w[lane].pts : 0ull;
+        long long vi = lane < nw ? s_w[lane].items : 0ll;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long tp = __shfl_up_sync(0xffffffffu, vp, o);
-            int ti = __shfl_up_sync(0xffffffffu, vi, o);
+            const unsigned long long tp = __shfl_up_sync(0xffffffffu, vp, o);
+            const long long ti = __shfl_up_sync(0xffffffffu, vi, o);
             if (lane >= o) { vp += tp; vi += ti; }
         }
-        if (lane < nw) { s_pts[lane] = vp; s_items[lane] = vi; }
+        if (lane < nw) s_w[lane] = ScanPart{vp, vi};
+        if (lane == nw - 1) *s_tot = ScanPart{vp, vi};
     }
     __syncthreads();
-    unsigned long long off = ip - pts + (wid ? s_pts[wid - 1] : 0ull);
-    int woff = ii - items + (wid ? s_items[wid - 1] : 0);
-    for (int b = b0; b < b1; ++b) {
-        const uint32_t c = count[b];
-        cursor[b] = (uint32_t)off;
-        for (uint32_t s = 0; s < c; s += (uint32_t)chunk) {
-            if (woff < max_work) work[woff] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), 0);
-            ++woff;
-        }
-        off += c;
+    if (wid > 0) { ip += s_w[wid - 1].pts; ii += s_w[wid - 1].items; }
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(kScanThreads) k_scan_bricks(const uint32_t* __restrict__ count,
+                                                              uint32_t* __restrict__ cursor, int nbricks,
+                                                              ScanPart* __restrict__ part, int4* __restrict__ work,
+                                                              int* __restrict__ counters, int max_work, int chunk) {
+    __shared__ ScanPart s_w[32], s_tot;
+    const int b = blockIdx.x * kScanSpan + 4 * threadIdx.x;
+    uint4 c4 = make_uint4(0, 0, 0, 0);
+    if (b < nbricks) c4 = *reinterpret_cast<const uint4*>(count + b);
+    const uint32_t c[4] = {c4.x, c4.y, c4.z, c4.w};
+    unsigned long long pts = 0;
+    long long items = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        pts += c[k];
+        items += (c[k] + chunk - 1) / chunk;
     }
-    if (tid == T - 1) {
-        counters[0] = min(woff, max_work);
+    unsigned long long ip = pts;
+    long long ii = items;
+    block_scan2(ip, ii, s_w, &s_tot);
+    if (!WRITE) {
+        if (threadIdx.x == 0) part[blockIdx.x] = s_tot;
+        return;
+    }
+    unsigned long long off = part[blockIdx.x].pts + ip - pts;      // part: exclusive block offsets
+    long long woff = part[blockIdx.x].items + ii - items;
+    if (b < nbricks) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            cursor[b + k] = (uint32_t)off;
+            for (uint32_t s = 0; s < c[k]; s += (uint32_t)chunk) {
+                if (woff < max_work) work[woff] = make_int4(b + k, (int)(off + s), (int)min((uint32_t)chunk, c[k] - s), 0);
+                ++woff;
+            }
+            off += c[k];
+        }
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+        counters[0] = (int)min(woff, (long long)max_work);
         counters[1] = 0;
     }
+}
+
+// Exclusive scan of the per-block totals in place (one block; n <= 32 * kScanThreads).
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(ScanPart* __restrict__ part, int n) {
+    __shared__ ScanPart s_w[32], s_tot;
+    const int per = (n + kScanThreads - 1) / kScanThreads;
+    const int i0 = min(n, (int)threadIdx.x * per), i1 = min(n, i0 + per);
+    unsigned long long pts = 0;
+    long long items = 0;
+    for (int i = i0; i < i1; ++i) { pts += part[i].pts; items += part[i].items; }
+    unsigned long long ip = pts;
+    long long ii = items;
+    block_scan2(ip, ii, s_w, &s_tot);
+    unsigned long long op = ip - pts;
+    long long oi = ii - items;
+    for (int i = i0; i < i1; ++i) {
+        const ScanPart v = part[i];
+        part[i] = ScanPart{op, oi};
+        op += v.pts;
+        oi += v.items;
+    }
+}
+
+static void launch_scan(Plan& P, int nbricks) {
+    Workspace& w = P.ws;
+    const int nblk = (nbricks + kScanSpan - 1) / kScanSpan;
+    ScanPart* part = reinterpret_cast<ScanPart*>(w.scan_part);
+    k_scan_bricks<false><<<nblk, kScanThreads, 0, P.stream>>>(w.count, w.cursor, nbricks, part, w.work,
+                                                               w.counters, (int)P.max_work, P.chunk);
+    k_scan_parts<<<1, kScanThreads, 0, P.stream>>>(part, nblk);
+    k_scan_bricks<true><<<nblk, kScanThreads, 0, P.stream>>>(w.count, w.cursor, nbricks, part, w.work,
+                                                              w.counters, (int)P.max_work, P.chunk);
+    P.launches += 3;
 }
 
 // Orders each piece round-robin over bank classes, in place: the point of rank r in
@@ -432,8 +489,7 @@ static void bin_w(Plan& P, const BinArgs& a0, int nbricks, bool kc) {
     const dim3 grid((a.nH + 255) / 256, (unsigned)(M < 65535 ? M : 65535));
     if (kc) k_bin<W, false, true><<<grid, 256, 0, P.stream>>>(a, M);
     else k_bin<W, false, false><<<grid, 256, 0, P.stream>>>(a, M);
-    k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work,
-                                          P.chunk);
+    launch_scan(P, nbricks);
     a.count = w.cursor;
     const int hN = P.N / 2, tiles_x = (hN + 1 + 3) / 4, n_tiles = tiles_x * ((P.N + 1 + 7) / 8);
     const dim3 grid2((n_tiles + 7) / 8, (unsigned)(M < 65535 ? M : 65535));
@@ -467,9 +523,7 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
     a.scale = (float)(G / P.N);
     const long long blocks = (a.npts + 255) / 256;
     if (blocks == 0) {
-        k_scan_work<<<1, 1024, 0, P.stream>>>(w.count, w.cursor, nbricks, w.work, w.counters, (int)P.max_work,
-                                          P.chunk);
-        P.launches += 1;
+        launch_scan(P, nbricks);
         return cudaGetLastError();
     }
     switch (P.p.W) {
@@ -478,7 +532,7 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
         case 8: bin_w<8>(P, a, nbricks, kc); break;
         default: return cudaErrorInvalidValue;
     }
-    P.launches += 4;
+    P.launches += 3;
     return cudaGetLastError();
 }
 
@@ -576,38 +630,72 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
 #pragma unroll 2
         for (int q = 0; q < PPR; ++q) {
             const int i = PPR * r + q;
-            if (i >= my_n) continue;
-            const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
+            // the warp's 32 lanes take 32 consecutive points of the piece (one warp step)
+            const bool live = i < my_n;
+            uint32_t id = 0;
+            PointPos p{};
+            int base = -1;
+            if (live) {
+                id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
+                p = point_pos(a.geom[id >> kTBits], __ldg(&a.htab[id & ((1u << kTBits) - 1u)]), a.scale, a.halfG,
+                              a.G);
+                base = region_base<W, BZ>(p, lo0, lo1, lo2);
+                if (base < 0) atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
+            }
+            // rank among the lanes of this step with the same bank class (base mod 32):
+            // a point of rank s starts at window plane s (mod W), so points of one class
+            // take different planes (offset RG^2 = 4 banks at W = 6) at every tap step
+            // instead of repeating one bank together
+            const unsigned same = __match_any_sync(0xffffffffu, base >= 0 ? (base & 31) : -1 - lane);
+            if (base < 0) continue;
+            int sh = __popc(same & ((1u << lane) - 1u));
+            sh = sh < W ? sh : sh % W;
             const int m = (int)(id >> kTBits);
             const int t = (int)(id & ((1u << kTBits) - 1u));
-            const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
-            const int base = region_base<W, BZ>(p, lo0, lo1, lo2);
-            if (base < 0) {
-                atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
-                continue;
-            }
             const float2 wv = point_weight(a, CPLX, m, t, (uint32_t)wk.y, s0 + kSpreadThreads * i);
             float wx[W], wy[W], wz[W];
             window_taps<W>(poly, p.f[0], wx);
             window_taps<W>(poly, p.f[1], wy);
             window_taps<W>(poly, p.f[2], wz);
-            const float wr = wv.x * S, wi = wv.y * S;
             const float dth = CPLX ? 0.0f : point_dither(id);
 #pragma unroll
-            for (int dz = 0; dz < W; ++dz) {
-                const float az = wr * wz[dz], bzw = wi * wz[dz];
+            for (int r = 1; r < W; ++r)
+                if (r <= sh) {
+                    const float t0 = wz[0];
+#pragma unroll
+                    for (int k = 0; k < W - 1; ++k) wz[k] = wz[k + 1];
+                    wz[W - 1] = t0;
+                }
+            const float2 w2 = make_float2(wv.x * S, wv.y * S);
+            const float2 magic2 = make_float2(kMagic, kMagic);
+            const float2 d2 = make_float2(dth, dth);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const int dz = k + sh < W ? k + sh : k + sh - W;
+                const float2 abz = __fmul2_rn(w2, make_float2(wz[k], wz[k]));
+                int* plane = lev1 + base + dz * (RG * RG);
 #pragma unroll
                 for (int dy = 0; dy < W; ++dy) {
-                    const float ayz = az * wy[dy], byz = bzw * wy[dy];
-                    int* row = lev1 + base + (dz * RG + dy) * RG;
+                    const float2 abyz = __fmul2_rn(abz, make_float2(wy[dy], wy[dy]));
+                    int* row = plane + dy * RG;
+                    if (CPLX) {
 #pragma unroll
-                    for (int dx = 0; dx < W; ++dx) {
-                        if (CPLX) {
-                            atomicAdd(row + dx, __float_as_int(fmaf(ayz, wx[dx], kMagic)) - kMagicBits);
-                            atomicAdd(row + RG3 + dx, __float_as_int(fmaf(byz, wx[dx], kMagic)) - kMagicBits);
-                        } else {
-                            atomicAdd(row + dx, __float_as_int(__fadd_rn(fmaf(ayz, wx[dx], dth), kMagic)) - kMagicBits);
+                        for (int dx = 0; dx < W; ++dx) {
+                            const float2 v = __ffma2_rn(abyz, make_float2(wx[dx], wx[dx]), magic2);
+                            atomicAdd(row + dx, __float_as_int(v.x) - kMagicBits);
+                            atomicAdd(row + RG3 + dx, __float_as_int(v.y) - kMagicBits);
                         }
+                    } else {
+                        const float2 a2 = make_float2(abyz.x, abyz.x);
+#pragma unroll
+                        for (int dx = 0; dx + 1 < W; dx += 2) {
+                            const float2 v = __fadd2_rn(__ffma2_rn(a2, make_float2(wx[dx], wx[dx + 1]), d2), magic2);
+                            atomicAdd(row + dx, __float_as_int(v.x) - kMagicBits);
+                            atomicAdd(row + dx + 1, __float_as_int(v.y) - kMagicBits);
+                        }
+                        if (W & 1)
+                            atomicAdd(row + W - 1,
+                                      __float_as_int(__fadd_rn(fmaf(abyz.x, wx[W - 1], dth), kMagic)) - kMagicBits);
                     }
                 }
             }
@@ -650,7 +738,7 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
 }
 
 template <int W, bool CPLX>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
+__global__ void __launch_bounds__(kSpreadThreads, CPLX ? 5 : 6) k_spread(const SpreadArgs a) {
     constexpr int NC = CPLX ? 2 : 1;
     constexpr int R3 = (kBrick + W) * (kBrick + W) * (Brick<!CPLX>::BZ + W);
     extern __shared__ int sm_i[];
@@ -673,7 +761,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(const SpreadArgs a) {
 // Persistent spreading over the work items of several plans: one queue, items of plan
 // p numbered item_off[p] .. item_off[p + 1] - 1 (plans in the order given).
 template <int W, bool CPLX>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread_batch(const SpreadArgs* __restrict__ desc, int n,
+__global__ void __launch_bounds__(kSpreadThreads, CPLX ? 5 : 6) k_spread_batch(const SpreadArgs* __restrict__ desc, int n,
                                                                  const int* __restrict__ item_off, int* queue,
                                                                  const KbPoly poly) {
     constexpr int NC = CPLX ? 2 : 1;
