@@ -522,9 +522,25 @@ __global__ void __launch_bounds__(kThreads) k_image_dft(const ImgArgs a) {
         auto st = [&](int line, int k, float2 v) { S1[k * H1 + c0 + line] = v; };
         block_fft<N, -1, true>(nl, ld, st, scr, a.tw);
     }
-    // half-disc samples: centred index sign, CTF, shift phase, k = 0 halved
+    // half-disc samples: centred index sign, CTF, shift phase, k = 0 halved.  The shift
+    // phase exp(i pi (k1 s1 + k2 s2)) factors per axis: its N/2 + 1 values in k1 and N + 1
+    // in k2 are formed once per image (in the scratch space, free after the columns)
     const int g = a.gid ? min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1) : 0;
     const float s1 = (float)(2.0 * a.shifts[2 * m] / N), s2 = (float)(2.0 * a.shifts[2 * m + 1] / N);
+    static_assert(img_smem_elems<N>() - N * H1 >= H1 + N + 1, "phase tables fit the scratch space");
+    float2* ph1 = scr;                  // k1 = 0 .. N/2
+    float2* ph2 = scr + H1;             // k2 = -N/2 .. N/2 at k2 + N/2
+    for (int j = threadIdx.x; j < H1 + N + 1; j += blockDim.x) {
+        float sn, cs;
+        if (j < H1) {
+            sincospif((float)j * s1, &sn, &cs);
+            ph1[j] = make_float2(cs, sn);
+        } else {
+            sincospif((float)(j - H1 - N / 2) * s2, &sn, &cs);
+            ph2[j - H1] = make_float2(cs, sn);
+        }
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < a.nH; t += blockDim.x) {
         const int kk = __ldg(&a.htab[t]);
         const int k1 = (int16_t)(kk & 0xffff), k2 = kk >> 16;
@@ -532,10 +548,8 @@ __global__ void __launch_bounds__(kThreads) k_image_dft(const ImgArgs a) {
         float hs = a.plain ? 1.0f : __ldg(&a.h1[(size_t)g * a.nH + t]);
         if ((k1 + k2) & 1) hs = -hs;
         if (t == 0 && !a.plain) hs *= 0.5f;
-        float sn, cs;
-        sincospif((float)k1 * s1 + (float)k2 * s2, &sn, &cs);
-        const float2 ph = make_float2(cs * hs, sn * hs);
-        a.samples[(size_t)m * a.nH + t] = c_mul(v, ph);
+        const float2 p = c_mul(ph1[k1], ph2[k2 + N / 2]);
+        a.samples[(size_t)m * a.nH + t] = c_mul(v, make_float2(p.x * hs, p.y * hs));
     }
 }
 
