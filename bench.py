@@ -674,7 +674,7 @@ def main():
             rec.pc_target(tgt)
         train_info["table_vs_target_mse"] = float(((tab - tgt) ** 2).mean())
 
-    def timed(n_steps):
+    def timed(n_steps, label="firm_step"):
         """n_steps steps between CUDA events on the plan's stream, stage events recorded
         (no extra host synchronisation); returns (ms per step, stage ms, iterations,
         launches, clocks)."""
@@ -688,7 +688,7 @@ def main():
         with ClockSampler(torch.cuda.current_device()) as clk:
             e0.record(stream)
             for _ in range(n_steps):
-                torch.cuda.nvtx.range_push("firm_step")    # lets a profiler select the timed steps
+                torch.cuda.nvtx.range_push(label)          # lets a profiler select the timed steps
                 _, it_ = step(R, gid, sh, img, x)
                 torch.cuda.nvtx.range_pop()
                 its.append(it_)
@@ -709,7 +709,7 @@ def main():
     mode["fused"] = not fused
     for _ in range(2):
         step(R, gid, sh, img, x)
-    ms_other, stages_other, _, _, _ = timed(max(2, min(args.steps, 5)))
+    ms_other, stages_other, _, _, _ = timed(max(2, min(args.steps, 5)), "firm_step_other_form")
     mode["fused"] = fused
     step(R, gid, sh, img, x)
     torch.cuda.synchronize(dev)
@@ -791,11 +791,17 @@ def main():
         kname = f"k_spread<{W},{'complex' if dom == 'spread_rhs' else 'real'}>"
     peak = 152 * 32 * 2.07e9
     achieved = atoms / (stages[dom] * 1e-3)
+    # DRAM bytes of one launch from an ncu capture of this workload (committed with the
+    # hash of the spreading source it was taken on; null once that source has changed)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "spread_traffic.json")
     if os.path.exists(prof) and (N, M, W) == (128, 50000, 6):   # the figure is for this workload
         try:
-            traffic = json.load(open(prof)).get(kname)
+            import hashlib
+            rec_t = json.load(open(prof)).get(kname) or {}
+            src = open(os.path.join(ROOT, "paper_1307_5824_gb300", "csrc", "spread.cu"), "rb").read()
+            if rec_t.get("source_sha256") == hashlib.sha256(src).hexdigest():
+                traffic = rec_t.get("dram_bytes")
         except Exception:
             traffic = None
     # the spreading pass against HBM (not its binding bound): algorithmic bytes = point ids
