@@ -882,38 +882,69 @@ __device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const Kb
 #pragma unroll 1
         for (int q = 0; q < PPR; ++q) {
             const int i = PPR * r + q;
-            if (i >= my_n) continue;
-            const uint32_t pos = s0 + T * i;
-            const uint32_t id = __ldg(&a.payload[pos]);
+            const bool live = i < my_n;
+            uint32_t id = 0;
+            PointPos p{};
+            int base = -1;
+            if (live) {
+                id = __ldg(&a.payload[s0 + T * i]);
+                p = point_pos(a.geom[id >> kTBits], __ldg(&a.htab[id & ((1u << kTBits) - 1u)]), a.scale, a.halfG,
+                              a.G);
+                base = region_base<W, BZ>(p, lo0, lo1, lo2);
+                if (base < 0) atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
+            }
+            // repeated bank classes in a warp step start at different window planes, as
+            // in spread_piece
+            const unsigned same = __match_any_sync(0xffffffffu, base >= 0 ? (base & 31) : -1 - lane);
+            if (base < 0) continue;
+            int sh = __popc(same & ((1u << lane) - 1u));
+            sh = sh < W ? sh : sh % W;
             const int m = (int)(id >> kTBits);
             const int t = (int)(id & ((1u << kTBits) - 1u));
-            const PointPos p = point_pos(a.geom[m], __ldg(&a.htab[t]), a.scale, a.halfG, a.G);
-            const int base = region_base<W, BZ>(p, lo0, lo1, lo2);
-            if (base < 0) {
-                atomicOr(&a.counters[2], 1);   // point outside its brick: reported, never written
-                continue;
-            }
             const int g = min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1);
             const float wk2 = __ldg(&a.h2[(size_t)g * a.nH + t]) * Sk;
             const float2 wv = __ldg(&a.samples[(size_t)m * a.nH + t]);
-            const float wr = wv.x * Sb, wi = wv.y * Sb;
+            const float2 w2 = make_float2(wv.x * Sb, wv.y * Sb);
             const float dth = point_dither(id);
             float wx[W], wy[W], wz[W];
             window_taps<W>(poly, p.f[0], wx);
             window_taps<W>(poly, p.f[1], wy);
             window_taps<W>(poly, p.f[2], wz);
 #pragma unroll
-            for (int dz = 0; dz < W; ++dz) {
-                const float kz = wk2 * wz[dz], az = wr * wz[dz], bzw = wi * wz[dz];
+            for (int rr = 1; rr < W; ++rr)
+                if (rr <= sh) {
+                    const float t0 = wz[0];
+#pragma unroll
+                    for (int k = 0; k < W - 1; ++k) wz[k] = wz[k + 1];
+                    wz[W - 1] = t0;
+                }
+            const float2 magic2 = make_float2(kMagic, kMagic);
+            const float2 d2 = make_float2(dth, dth);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const int dz = k + sh < W ? k + sh : k + sh - W;
+                const float kz = wk2 * wz[k];
+                const float2 abz = __fmul2_rn(w2, make_float2(wz[k], wz[k]));
+                int* plane = lev1 + base + dz * (RG * RG);
 #pragma unroll
                 for (int dy = 0; dy < W; ++dy) {
-                    const float kyz = kz * wy[dy], ayz = az * wy[dy], byz = bzw * wy[dy];
-                    int* row = lev1 + base + (dz * RG + dy) * RG;
+                    const float kyz = kz * wy[dy];
+                    const float2 abyz = __fmul2_rn(abz, make_float2(wy[dy], wy[dy]));
+                    int* row = plane + dy * RG;
+                    const float2 k2 = make_float2(kyz, kyz);
+#pragma unroll
+                    for (int dx = 0; dx + 1 < W; dx += 2) {
+                        const float2 v = __fadd2_rn(__ffma2_rn(k2, make_float2(wx[dx], wx[dx + 1]), d2), magic2);
+                        atomicAdd(row + dx, __float_as_int(v.x) - kMagicBits);
+                        atomicAdd(row + dx + 1, __float_as_int(v.y) - kMagicBits);
+                    }
+                    if (W & 1)
+                        atomicAdd(row + W - 1, __float_as_int(__fadd_rn(fmaf(kyz, wx[W - 1], dth), kMagic)) - kMagicBits);
 #pragma unroll
                     for (int dx = 0; dx < W; ++dx) {
-                        atomicAdd(row + dx, __float_as_int(__fadd_rn(fmaf(kyz, wx[dx], dth), kMagic)) - kMagicBits);
-                        atomicAdd(row + RG3 + dx, __float_as_int(fmaf(ayz, wx[dx], kMagic)) - kMagicBits);
-                        atomicAdd(row + 2 * RG3 + dx, __float_as_int(fmaf(byz, wx[dx], kMagic)) - kMagicBits);
+                        const float2 v = __ffma2_rn(abyz, make_float2(wx[dx], wx[dx]), magic2);
+                        atomicAdd(row + RG3 + dx, __float_as_int(v.x) - kMagicBits);
+                        atomicAdd(row + 2 * RG3 + dx, __float_as_int(v.y) - kMagicBits);
                     }
                 }
             }
