@@ -93,6 +93,7 @@ def parse():
                          "is timed beside it either way")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-c4", action="store_true", help="skip the batched (64-reconstruction) leg")
     ap.add_argument("--oracle-single", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--spread-only", action="store_true",
                     help="profiling: the separate channels (firm_kernel + firm_backproject) twice, then the fused "
@@ -366,6 +367,14 @@ def run_reference(args):
 # the batched form (64 reconstructions per step)
 # ---------------------------------------------------------------------------
 def run_batched(args):
+    out = batched_result(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+def batched_result(args):
+    """The batched form (64 reconstructions of uneven size): its JSON record on rank 0,
+    None on the other ranks."""
     import multiprocessing as mp
 
     import synth
@@ -509,7 +518,7 @@ def run_batched(args):
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
-        return
+        return None
     pts = sum(it["M"] * disc_size(r.N) for r, it in zip(recs, items))
     out = {"metric": "batched FIRM reconstructions/s (64 recon, N in {48,64,80,96}, 1k-8k images, 25 CG iterations)",
            "value": n * world / (ms / 1e3), "unit": "recon/s", "n_gpus": world, "steps": args.steps,
@@ -528,12 +537,12 @@ def run_batched(args):
            "gpu_launches": int(B.launch_count() * args.steps),
            "e2e": {"value": n / e2e_s, "unit": "recon/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
            "clocks": clk.summary(), "synth_s": round(t_syn, 1)}
-    print(json.dumps(out))
     B.close()
     for r in recs:
         r.close()
     if world > 1:
         dist.destroy_process_group()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -729,11 +738,14 @@ def main():
     if not args.no_e2e:
         x_h = torch.empty((N, N, N), dtype=torch.float32).pin_memory()
 
-        # the two forms alternate step by step (same drift for both); the upload staged
-        # ahead overlaps the binning (fused) or the kernel channel (separate)
+        # both channel forms, each with the upload staged ahead and in stream order,
+        # alternating step by step (the same drift for all four); the staged upload
+        # overlaps the binning (fused) or the whole kernel channel (separate)
         n_e2e = max(args.steps, 5)
-        res = {False: 0.0, True: 0.0}
-        for staged in (False, True):            # one untimed step of each form
+        variants = [(f, staged) for f in (fused, not fused) for staged in (False, True)]
+        res = {v: 0.0 for v in variants}
+        for f, staged in variants:               # one untimed step of each
+            mode["fused"] = f
             if staged:
                 rec.stage_images(img_h)
             step(R_h, g_h, s_h, img_h, x_h)
@@ -741,21 +753,27 @@ def main():
         if world > 1:
             dist.barrier()
         for _ in range(n_e2e):
-            for staged in (False, True):
+            for f, staged in variants:
+                mode["fused"] = f
                 t0 = time.perf_counter()
                 if staged:
                     rec.stage_images(img_h)
                 step(R_h, g_h, s_h, img_h, x_h)
                 torch.cuda.synchronize(dev)
-                res[staged] += time.perf_counter() - t0
-        _, (serial_s, staged_s) = job_time([res[False] / n_e2e, res[True] / n_e2e], world, dev)
-        res = {False: serial_s, True: staged_s}
+                res[(f, staged)] += time.perf_counter() - t0
+        mode["fused"] = fused
+        _, times = job_time([res[v] / n_e2e for v in variants], world, dev)
+        res = dict(zip(variants, times))
         h2d = R_h.numel() * 8 + g_h.numel() * 4 + s_h.numel() * 8 + img_h.numel() * 2
-        e2e = {"value": res[True], "unit": "s/recon", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(x_h.numel() * 4),
-               "upload": "staged ahead (firm_stage_images), overlapped with the binning" if fused else
+        # the user's call for host-resident inputs is the faster form with the upload staged
+        best = min((fused, not fused), key=lambda f: res[(f, True)])
+        name = lambda f: "fused" if f else "separate"
+        e2e = {"value": res[(best, True)], "unit": "s/recon", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(x_h.numel() * 4), "form": name(best) + " channels",
+               "upload": "staged ahead (firm_stage_images), overlapped with the binning" if best else
                          "staged ahead (firm_stage_images), overlapped with the kernel channel",
-               "value_serial_upload": res[False]}
+               "value_serial_upload": res[(best, False)],
+               "by_form": {name(f) + ("_staged" if st else "_serial"): res[(f, st)] for f, st in variants}}
 
     # the same reconstruction with plain CG (the comparison the metric names)
     plain = None
@@ -943,6 +961,24 @@ def main():
         "learned_training": train_info,
         "plain_cg": plain,
     }
+    # the batched form (64 reconstructions of uneven N and image count, one graph launch
+    # per step; to rel-res 1e-4 with the batch's network) on the same GPU, after this
+    # workload's buffers are released
+    if world == 1 and args.workload == WORKLOAD and args.images is None and not (args.no_c4 or args.no_compare):
+        rec.close()
+        del img, img_h, R, R_h, x
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        try:
+            c4_args = argparse.Namespace(**vars(args))
+            c4_args.steps, c4_args.warmup, c4_args.batch = 3, 3, None
+            c4 = batched_result(c4_args)
+            out["batched_c4"] = {k: c4[k] for k in ("metric", "value", "unit", "ms_per_step", "tuned", "ms_no_graph",
+                                                    "ms_sequential_single_plan", "speedup_vs_sequential",
+                                                    "cg_status_ok", "to_rel_res_1e-4", "e2e", "gpu_launches",
+                                                    "clocks", "config")}
+        except Exception as exc:                     # reported, never fatal to the main line
+            out["batched_c4"] = {"error": f"{type(exc).__name__}: {exc}"}
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
