@@ -135,6 +135,21 @@ __device__ __forceinline__ float point_dither(uint32_t id) {
     return (float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f;
 }
 
+// Rank (mod W) of this lane's point among the lanes of its warp with the same bank
+// class (base mod 32; base < 0: no point).  Called by all 32 lanes.  Most warp steps of
+// a round-robin piece hold 32 distinct classes: one OR-reduction of the class bits
+// finds those, and only the others pay for the match.
+template <int W>
+__device__ __forceinline__ int class_rank(int base, int lane) {
+    const bool pt = base >= 0;
+    const unsigned bits = __reduce_or_sync(0xffffffffu, pt ? 1u << (base & 31) : 0u);
+    const unsigned pts = __ballot_sync(0xffffffffu, pt);
+    if (__popc(bits) == __popc(pts)) return 0;
+    const unsigned same = __match_any_sync(0xffffffffu, pt ? (base & 31) : -1 - lane);
+    const int r = __popc(same & ((1u << lane) - 1u));
+    return r < W ? r : r % W;
+}
+
 // Bricks: 8 x 8 x BZ cells (BZ = kBrickZk for the kernel channel, 8 for A*b).
 template <bool KC> struct Brick { static constexpr int BZ = KC ? kBrickZk : kBrick; };
 
@@ -646,10 +661,8 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
             // a point of rank s starts at window plane s (mod W), so points of one class
             // take different planes (offset RG^2 = 4 banks at W = 6) at every tap step
             // instead of repeating one bank together
-            const unsigned same = __match_any_sync(0xffffffffu, base >= 0 ? (base & 31) : -1 - lane);
+            const int sh = class_rank<W>(base, lane);
             if (base < 0) continue;
-            int sh = __popc(same & ((1u << lane) - 1u));
-            sh = sh < W ? sh : sh % W;
             const int m = (int)(id >> kTBits);
             const int t = (int)(id & ((1u << kTBits) - 1u));
             const float2 wv = point_weight(a, CPLX, m, t, (uint32_t)wk.y, s0 + kSpreadThreads * i);
@@ -895,10 +908,8 @@ __device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const Kb
             }
             // repeated bank classes in a warp step start at different window planes, as
             // in spread_piece
-            const unsigned same = __match_any_sync(0xffffffffu, base >= 0 ? (base & 31) : -1 - lane);
+            const int sh = class_rank<W>(base, lane);
             if (base < 0) continue;
-            int sh = __popc(same & ((1u << lane) - 1u));
-            sh = sh < W ? sh : sh % W;
             const int m = (int)(id >> kTBits);
             const int t = (int)(id & ((1u << kTBits) - 1u));
             const int g = min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1);
