@@ -622,11 +622,20 @@ __device__ __forceinline__ void spread_piece(const SpreadArgs& a, const KbPoly& 
     const int my_n = wk.z > (int)threadIdx.x ? (wk.z - (int)threadIdx.x + kSpreadThreads - 1) / kSpreadThreads : 0;
     float wmax = a.wmax_fixed;
     if (wmax <= 0.0f) {
-        for (int i = 0; i < my_n; ++i) {
-            const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
-            const float2 wv = point_weight(a, CPLX, (int)(id >> kTBits), (int)(id & ((1u << kTBits) - 1u)),
-                                           (uint32_t)wk.y, s0 + kSpreadThreads * i);
-            wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+        if (CPLX) {
+            // the piece's A*b weights sit in its own window of samples_b (scatter order):
+            // read it straight, coalesced, instead of through the ids and permutation
+            for (int j = threadIdx.x; j < wk.z; j += kSpreadThreads) {
+                const float2 wv = __ldg(&a.samples_b[wk.y + j]);
+                wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+            }
+        } else {
+            for (int i = 0; i < my_n; ++i) {
+                const uint32_t id = __ldg(&a.payload[s0 + kSpreadThreads * i]);
+                const float2 wv = point_weight(a, CPLX, (int)(id >> kTBits), (int)(id & ((1u << kTBits) - 1u)),
+                                               (uint32_t)wk.y, s0 + kSpreadThreads * i);
+                wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
