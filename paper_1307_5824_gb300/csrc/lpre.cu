@@ -56,42 +56,46 @@ __global__ void __launch_bounds__(1024) k_view_moment(const double* __restrict__
 }
 
 // h^2-weighted histogram of the half-disc samples (the mirrored half falls in the same
-// bin).  A thread owns one sample t of every image its block visits: |xi| = |k| fixes
-// the shell, so only the cone moves with the image, and the thread sums its weights
-// per cone in registers (|<xi, a>| = |k1 <u, a> + k2 <v, a>| with u, v the slice axes)
-// and adds them to the block's histogram once.
-__global__ void __launch_bounds__(256) k_pc_features(const ImgGeom* __restrict__ geom, const int32_t* __restrict__ htab,
-                                                     const int32_t* __restrict__ gid, const float* __restrict__ h2,
-                                                     int M, int nH, int n_ctf, float halfN,
-                                                     const float* __restrict__ axis, float* __restrict__ hist) {
-    const float a1 = axis[0], a2 = axis[1], a3 = axis[2];
+// bin).  A thread owns one image and walks a range of samples t (blockIdx.y picks the
+// range): |xi| = |k| fixes the shell and the cone only needs |k1 <u, a> + k2 <v, a>| /
+// |k| (u, v the slice axes, a the viewing axis), so the block first tabulates, per t of
+// its range, the shell and k / |k|, and every point is then two FMAs, a cone index and
+// one shared-memory atomic into the block's histogram.
+constexpr int kFeatThreads = 256;
+constexpr int kFeatT = 1024;          // samples t per block (the table: 12 B each)
+__global__ void __launch_bounds__(kFeatThreads) k_pc_features(const ImgGeom* __restrict__ geom,
+                                                              const int32_t* __restrict__ htab,
+                                                              const int32_t* __restrict__ gid,
+                                                              const float* __restrict__ h2, int M, int nH, int n_ctf,
+                                                              float halfN, const float* __restrict__ axis,
+                                                              float* __restrict__ hist) {
     __shared__ float s_h[kBins];
+    __shared__ float2 s_k[kFeatT];        // k / |k| (0 at k = 0)
+    __shared__ int s_s[kFeatT];           // shell of t
+    const float a1 = axis[0], a2 = axis[1], a3 = axis[2];
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_h[i] = 0.0f;
-    __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < nH) {
-        const int kk = htab[t];
+    const int t0 = blockIdx.y * kFeatT, t1 = min(nH, t0 + kFeatT);
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const int kk = __ldg(&htab[t]);
         const float k1 = (float)(int16_t)(kk & 0xffff), k2 = (float)(kk >> 16);
         const float rk = sqrtf(k1 * k1 + k2 * k2);     // |xi| in grid units, exactly |k|
-        const int s = min(kShells - 1, (int)floorf((float)kShells * rk / halfN));
         const float inv_r = rk > 0.0f ? 1.0f / rk : 0.0f;
-        float acc[kCones];
-#pragma unroll
-        for (int j = 0; j < kCones; ++j) acc[j] = 0.0f;
-        for (int m = blockIdx.y; m < M; m += gridDim.y) {
-            const ImgGeom g = geom[m];
-            const float ua = g.uh[0] * a1 + g.uh[1] * a2 + g.uh[2] * a3;
-            const float va = g.vh[0] * a1 + g.vh[1] * a2 + g.vh[2] * a3;
-            const float c = fabsf(k1 * ua + k2 * va) * inv_r;
-            const int cb = min(kCones - 1, (int)floorf((float)kCones * c));
-            const int gg = min(max(gid[m], 0), n_ctf - 1);
-            const float w = __ldg(&h2[(size_t)gg * nH + t]);
-#pragma unroll
-            for (int j = 0; j < kCones; ++j) acc[j] += (j == cb) ? w : 0.0f;
+        s_k[t - t0] = make_float2(k1 * inv_r, k2 * inv_r);
+        s_s[t - t0] = min(kShells - 1, (int)floorf((float)kShells * rk / halfN));
+    }
+    __syncthreads();
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) {
+        const ImgGeom g = geom[m];
+        const float ua = g.uh[0] * a1 + g.uh[1] * a2 + g.uh[2] * a3;
+        const float va = g.vh[0] * a1 + g.vh[1] * a2 + g.vh[2] * a3;
+        const float* h2g = h2 + (size_t)min(max(gid[m], 0), n_ctf - 1) * nH;
+        for (int t = t0; t < t1; ++t) {
+            const float2 kr = s_k[t - t0];
+            const float c = fabsf(fmaf(kr.x, ua, kr.y * va));
+            const int cb = min(kCones - 1, (int)((float)kCones * c));
+            atomicAdd(&s_h[kCones * s_s[t - t0] + cb], __ldg(&h2g[t]));
         }
-#pragma unroll
-        for (int j = 0; j < kCones; ++j)
-            if (acc[j] != 0.0f) atomicAdd(&s_h[kCones * s + j], acc[j]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kBins; i += blockDim.x)
@@ -198,9 +202,9 @@ cudaError_t launch_view_axis(Plan& P, const double* R, int M) {
 cudaError_t launch_pc_features(Plan& P, int M, float* hist) {
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(float) * kBins, P.stream);
     if (e != cudaSuccess || M <= 0) return e;
-    const dim3 grid((P.nH + 255) / 256, (unsigned)(M < 256 ? M : 256));
-    k_pc_features<<<grid, 256, 0, P.stream>>>(P.ws.geom, P.ws.htab, P.cur_gid, P.ws.h2, M, P.nH, P.n_ctf, 0.5f * P.N,
-                                              P.ws.axis, hist);
+    const dim3 grid((M + kFeatThreads - 1) / kFeatThreads, (P.nH + kFeatT - 1) / kFeatT);
+    k_pc_features<<<grid, kFeatThreads, 0, P.stream>>>(P.ws.geom, P.ws.htab, P.cur_gid, P.ws.h2, M, P.nH, P.n_ctf,
+                                                       0.5f * P.N, P.ws.axis, hist);
     P.launches += 1;
     return cudaGetLastError();
 }
