@@ -358,8 +358,8 @@ int firm_toeplitz_apply(firm_plan_t plan, const float* x, float* y);
  * All four pointers must be memory of the current device; anything else is rejected
  * with FIRM_EINVAL.  The first call on a device does a one-time set-up: it looks up the
  * array's device address and writes the FFT twiddles of every supported N into it with
- * a synchronous copy (once per device, under a lock); make that first call before any
- * stream capture.  Later calls only queue kernels.  All calls share the one array:
+ * a synchronous copy (once per device, under a lock), so that first call waits for the
+ * device.  Later calls only queue kernels.  All calls share the one array:
  * calls whose work overlaps on the GPU (other streams, other threads) race and must be
  * serialised by the caller.  Every pass writes its scratch before reading it, so
  * nothing has to start at zero. */
