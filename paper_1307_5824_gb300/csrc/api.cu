@@ -170,6 +170,7 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     w.count = c.take<uint32_t>(nb3);
     w.cursor = c.take<uint32_t>(nb3);
     w.work = c.take<int4>(max_work);
+    w.wmax_item = c.take<float>(max_work);
     w.scan_part = c.take<unsigned long long>(2 * (nb3 / kScanSpan + 1));
     w.item_part = c.take<double>(2 * max_work);
     w.counters = c.take<int>(8);

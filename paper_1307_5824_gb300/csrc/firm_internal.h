@@ -86,6 +86,7 @@ struct Workspace {
     float2* samples_b = nullptr;    // A*b weights in scatter order (written by the scatter pass)
     uint16_t* perm = nullptr;       // per payload position: index in scatter order within its piece
     int4* work = nullptr;           // (brick, start, count, -)
+    float* wmax_item = nullptr;     // fused form: per work item, the largest |h b| of its points
     unsigned long long* scan_part = nullptr;   // brick scan: per-block (points, items) totals
     double* item_part = nullptr;    // per work item: two FP64 partial sums (data residual)
     int* counters = nullptr;        // [0] work items, [1] work cursor, [2] error flag

@@ -577,6 +577,7 @@ struct SpreadArgs {
     int G, halfG, nb, nH, n_ctf;
     float scale;
     float wmax_fixed;         // > 0: bound on |w| known in advance (no pre-pass)
+    const float* wmax_item;   // fused form: per work item, the largest |h b| of its points
     KbPoly poly;
 };
 
@@ -865,34 +866,21 @@ template <int T> struct FusedRound {
 };
 
 template <int W, int T>
-__device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const KbPoly& poly, const int4 wk, int* lev1,
-                                                   float* lev2, float* s_red) {
-    constexpr int kWarps = T / 32;
+__device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const KbPoly& poly, const int item,
+                                                   const int4 wk, int* lev1, float* lev2) {
     constexpr int BZ = kBrickZk;
     constexpr int RG = kBrick + W;
     constexpr int RG3 = RG * RG * (BZ + W);
     constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
     constexpr int kMagicBits = 0x4B400000;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int b = wk.x;
     const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
     const int lo0 = bx * kBrick, lo1 = by * kBrick, lo2 = bz * BZ;
     const uint32_t s0 = (uint32_t)wk.y + threadIdx.x;
     const int my_n = wk.z > (int)threadIdx.x ? (wk.z - (int)threadIdx.x + T - 1) / T : 0;
-    // largest |h b| of the piece (the A*b scale)
-    float wmax = 0.0f;
-    for (int i = 0; i < my_n; ++i) {
-        const uint32_t id = __ldg(&a.payload[s0 + T * i]);
-        const float2 wv = __ldg(&a.samples[(size_t)(id >> kTBits) * a.nH + (id & ((1u << kTBits) - 1u))]);
-        wmax = fmaxf(wmax, fmaxf(fabsf(wv.x), fabsf(wv.y)));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-    if (lane == 0) s_red[warp] = wmax;
-    __syncthreads();
-    wmax = s_red[0];
-#pragma unroll
-    for (int i = 1; i < kWarps; ++i) wmax = fmaxf(wmax, s_red[i]);
+    // largest |h b| of the piece (the A*b scale), found by the gather pass
+    const float wmax = __ldg(&a.wmax_item[item]);
     constexpr int PPR = FusedRound<T>::PPR, SB = FusedRound<T>::kScaleBits;
     const int rounds = (((wk.z + T - 1) / T) + PPR - 1) / PPR;
     int ek = 0, eb = 0;
@@ -923,7 +911,7 @@ __device__ __forceinline__ void spread_piece_fused(const SpreadArgs& a, const Kb
             const int t = (int)(id & ((1u << kTBits) - 1u));
             const int g = min(max(__ldg(&a.gid[m]), 0), a.n_ctf - 1);
             const float wk2 = __ldg(&a.h2[(size_t)g * a.nH + t]) * Sk;
-            const float2 wv = __ldg(&a.samples[(size_t)m * a.nH + t]);
+            const float2 wv = __ldg(&a.samples_b[s0 + T * i]);     // gathered in payload order
             const float2 w2 = make_float2(wv.x * Sb, wv.y * Sb);
             const float dth = point_dither(id);
             float wx[W], wy[W], wz[W];
@@ -1012,7 +1000,6 @@ __global__ void __launch_bounds__(kFusedThreads) k_spread_fused(const SpreadArgs
     int* lev1 = sm_i;                                          // 3 * R3 int32
     float* lev2 = reinterpret_cast<float*>(sm_i + 3 * R3);     // 3 * R3 float
     __shared__ int s_item;
-    __shared__ float s_red[kFusedThreads / 32];
     for (int i = threadIdx.x; i < 6 * R3; i += blockDim.x) sm_i[i] = 0;
     const int n_work = a.counters[0];
     for (;;) {
@@ -1021,7 +1008,39 @@ __global__ void __launch_bounds__(kFusedThreads) k_spread_fused(const SpreadArgs
         __syncthreads();
         const int item = s_item;
         if (item >= n_work) break;
-        spread_piece_fused<W, kFusedThreads>(a, a.poly, a.work[item], lev1, lev2, s_red);
+        spread_piece_fused<W, kFusedThreads>(a, a.poly, item, a.work[item], lev1, lev2);
+    }
+}
+
+// The fused pass's A*b weights in payload order (samples_b[pos] = h b of the point at
+// pos, one gathered 8-byte read per point) and each work item's largest |h b| (its
+// fixed-point scale), so the spreading pass reads both coalesced.
+__global__ void __launch_bounds__(256) k_fused_gather(const uint32_t* __restrict__ payload,
+                                                      const int4* __restrict__ work, const int* __restrict__ counters,
+                                                      const float2* __restrict__ samples, int nH,
+                                                      float2* __restrict__ samples_b, float* __restrict__ wmax_item) {
+    __shared__ float s_red[8];
+    const int n_work = counters[0];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
+        const int4 wk = work[item];
+        float wmax = 0.0f;
+        for (int i = threadIdx.x; i < wk.z; i += blockDim.x) {
+            const uint32_t id = __ldg(&payload[wk.y + i]);
+            const float2 v = __ldg(&samples[(size_t)(id >> kTBits) * nH + (id & ((1u << kTBits) - 1u))]);
+            samples_b[wk.y + i] = v;
+            wmax = fmaxf(wmax, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        if (lane == 0) s_red[warp] = wmax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = s_red[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_red[w]);
+            wmax_item[item] = m;
+        }
+        __syncthreads();
     }
 }
 
@@ -1097,6 +1116,7 @@ static SpreadArgs spread_args(Plan& P, bool kc) {
     a.n_ctf = P.n_ctf;
     a.scale = (float)(G / P.N);
     a.wmax_fixed = kc ? P.h2_max : 0.0f;
+    a.wmax_item = nullptr;
     a.poly = P.poly;
     return a;
 }
@@ -1129,6 +1149,12 @@ cudaError_t launch_spread_fused(Plan& P, int M) {
     cudaError_t e = cudaMemsetAsync(P.ws.grid, 0, sizeof(double) * 3 * cells, P.stream);
     if (e != cudaSuccess || M <= 0) return e;
     SpreadArgs a = spread_args(P, true);
+    k_fused_gather<<<P.num_sms * 8, 256, 0, P.stream>>>(a.payload, a.work, a.counters, P.ws.samples, P.nH,
+                                                       P.ws.samples_b, P.ws.wmax_item);
+    P.launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    a.samples_b = P.ws.samples_b;
+    a.wmax_item = P.ws.wmax_item;
     switch (P.p.W) {
         case 6: return spread_fused_w<6>(P, a);
         case 7: return spread_fused_w<7>(P, a);
