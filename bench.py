@@ -86,7 +86,7 @@ def parse():
                          "RCT: random conical tilt (60 degrees), N=96, 10k images, SNR 1, with the FCR of the "
                          "solution inside and outside the missing cone")
     ap.add_argument("--batch", type=int, default=None, help="C4: reconstructions per batch (default 64)")
-    ap.add_argument("--channels", default="separate", choices=["fused", "separate"],
+    ap.add_argument("--channels", default="fused", choices=["fused", "separate"],
                     help="separate: firm_kernel then firm_backproject (the image upload of the end-to-end step "
                          "hides behind the whole kernel channel); fused: one binning and one spreading pass for Ker "
                          "and A*b (firm_kernel_backproject; only the binning can hide the upload).  The other form "
@@ -800,33 +800,42 @@ def main():
     # unit: one shared-memory atomic add: W^3 per half-disc point for the kernel channel,
     # 2 W^3 for A*b, 3 W^3 for the fused pass.  Peak: 152 SMs x 32 lanes x 2.07 GHz (one
     # warp-wide shared atomic per clock per SM) = 10.07e12 / s.
-    spread_ms = stages["spread_ker"] + stages["spread_rhs"]
-    if fused:
-        dom, atoms, kname = "spread_ker", M * nH * W ** 3 * 3, f"k_spread_fused<{W}>"
-    else:
-        dom = "spread_rhs" if stages["spread_rhs"] >= stages["spread_ker"] else "spread_ker"
-        atoms = M * nH * W ** 3 * (2 if dom == "spread_rhs" else 1)
-        kname = f"k_spread<{W},{'complex' if dom == 'spread_rhs' else 'real'}>"
-    peak = 152 * 32 * 2.07e9
-    achieved = atoms / (stages[dom] * 1e-3)
-    # DRAM bytes of one launch from an ncu capture of this workload (committed with the
-    # hash of the spreading source it was taken on; null once that source has changed)
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "spread_traffic.json")
-    if os.path.exists(prof) and (N, M, W) == (128, 50000, 6):   # the figure is for this workload
-        try:
-            import hashlib
-            rec_t = json.load(open(prof)).get(kname) or {}
-            src = open(os.path.join(ROOT, "paper_1307_5824_gb300", "csrc", "spread.cu"), "rb").read()
-            if rec_t.get("source_sha256") == hashlib.sha256(src).hexdigest():
-                traffic = rec_t.get("dram_bytes")
-        except Exception:
-            traffic = None
+    spread_ms = stages["spread_ker"] + stages["spread_rhs"] + stages.get("gather_fused", 0.0)
+
+    def roofline_of(st, is_fused):
+        """Shared-atomic rate of the dominant spreading kernel of one channel form, with
+        its DRAM bytes per launch from an ncu capture of this workload (committed with
+        the hash of the spreading source it was taken on; null once that source changed)."""
+        if is_fused:
+            dom, atoms, kname = "spread_ker", M * nH * W ** 3 * 3, f"k_spread_fused<{W}>"
+        else:
+            dom = "spread_rhs" if st["spread_rhs"] >= st["spread_ker"] else "spread_ker"
+            atoms = M * nH * W ** 3 * (2 if dom == "spread_rhs" else 1)
+            kname = f"k_spread<{W},{'complex' if dom == 'spread_rhs' else 'real'}>"
+        peak = 152 * 32 * 2.07e9
+        achieved = atoms / (st[dom] * 1e-3)
+        traffic = None
+        prof = os.path.join(ROOT, "profiles", "spread_traffic.json")
+        if os.path.exists(prof) and (N, M, W) == (128, 50000, 6):   # the figure is for this workload
+            try:
+                import hashlib
+                rec_t = json.load(open(prof)).get(kname) or {}
+                src = open(os.path.join(ROOT, "paper_1307_5824_gb300", "csrc", "spread.cu"), "rb").read()
+                if rec_t.get("source_sha256") == hashlib.sha256(src).hexdigest():
+                    traffic = rec_t.get("dram_bytes")
+            except Exception:
+                traffic = None
+        return {"kernel": kname, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "Tatomic/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 32 shared-atomic lanes/clk x 2.07 GHz"}
+
+    roofline = roofline_of(stages, fused)
+    roofline_other = roofline_of(stages_other, not fused)
     # the spreading pass against HBM (not its binding bound): algorithmic bytes = point ids
     # and weights read + the FP64 fine grids written once
     Gk, Gr = 4 * N, 2 * N
-    if fused:
-        spread_bytes = M * nH * (4 + 8) + 3 * Gk ** 3 * 8
+    if fused:   # the weight gather (ids, weights by id, weights in payload order) + the pass
+        spread_bytes = M * nH * (4 + 8 + 8) + M * nH * (4 + 8) + 3 * Gk ** 3 * 8
     else:
         spread_bytes = M * nH * 4 + Gk ** 3 * 8 + M * nH * (4 + 8 + 2) + Gr ** 3 * 16
     hbm_peak = None
@@ -948,10 +957,8 @@ def main():
             (stages_other if fused else stages).get(k, 0.0) for k in ("bin_ker", "spread_ker", "fft_ker", "khat")))
         / 1e3,
         "stage_ms": {k: round(v, 4) for k, v in stages.items() if k != "cg_iters"},
-        "roofline": {"kernel": kname, "bound": "alu",
-                     "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tatomic/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": "derived: 152 SMs x 32 shared-atomic lanes/clk x 2.07 GHz"},
+        "roofline": roofline,
+        ("roofline_separate_channels" if fused else "roofline_fused_channels"): roofline_other,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -405,6 +405,7 @@ int firm_bin_info(firm_plan_t plan, int* n_work, int* n_points, int* bricks_per_
  *   4 geometry + image DFT                  5 binning (A*b channel)
  *   6 spreading (A*b channel)               7 2N^3 transform + deconvolution (A*b)
  *   8 CG total                              9 CG iterations of the last solve
+ *  10 the fused form's weight gather (firm_kernel_backproject; its spreading is slot 1)
  * firm_stage_times waits for the recorded events and fills out[0..n-1]. */
 int firm_set_timing(firm_plan_t plan, int on);
 int firm_stage_times(firm_plan_t plan, double* out, int n);

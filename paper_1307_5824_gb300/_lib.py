@@ -281,7 +281,7 @@ def firm_set_timing(plan, on: bool):
 
 
 STAGES = ["bin_ker", "spread_ker", "fft_ker", "khat", "image_dft", "bin_rhs", "spread_rhs", "fft_rhs",
-          "cg", "cg_iters"]
+          "cg", "cg_iters", "gather_fused"]
 
 
 def firm_stage_times(plan) -> dict:

@@ -180,6 +180,9 @@ size_t layout_workspace(const firm_params& p, char* base, Workspace& w) {
     const size_t grid_bytes = std::max(Gk * Gk * Gk * sizeof(double) * (fused ? 3 : 1),
                                        Gr * Gr * Gr * 2 * sizeof(double));
     w.grid = c.take<double>(grid_bytes / sizeof(double));
+    // fused plans keep the kernel channel's ids in scatter order for the weight gather
+    w.payload_scat = fused ? c.take<uint32_t>(M * nH) : nullptr;
+    w.inv_perm = fused ? c.take<uint16_t>(M * nH) : nullptr;
     // union: staged images | point ids | FFT intermediates (never live together)
     const size_t fx1 = std::max({Gk * Gk * (N + 1), Gr * Gr * N, H3});
     const size_t fx2 = std::max({Gk * 2 * N * (N + 1), Gr * N * N, H3});
@@ -602,6 +605,7 @@ int firm_kernel(firm_plan_t plan, int M, const double* R, const int32_t* group, 
     if (group) P.cur_gid = stage(group, w.gid, (size_t)M, P.stream, e);
     else { e = cudaMemsetAsync(w.gid, 0, sizeof(int32_t) * (M > 0 ? M : 1), P.stream); P.cur_gid = w.gid; }
     FIRM_CK(e);
+    P.ev_used[10] = false;                     // no fused weight gather in this form
     FIRM_CK(start_stage(P));                   // a staged image upload runs beside the kernel channel
     P.bin_M = -1;
     tm.start(0);
@@ -728,6 +732,9 @@ int firm_kernel_backproject(firm_plan_t plan, int M, const void* images, const d
         FIRM_CK(launch_bin(P, M, true));
         tm.stop();
     }
+    tm.start(10);
+    FIRM_CK(launch_fused_gather(P, M));
+    tm.stop();
     tm.start(1);
     FIRM_CK(launch_spread_fused(P, M));
     tm.stop();

@@ -82,6 +82,8 @@ struct Workspace {
     uint32_t* count = nullptr;      // per brick
     uint32_t* cursor = nullptr;
     uint32_t* payload = nullptr;    // point ids m * nH + t sorted by brick, then bank class
+    uint32_t* payload_scat = nullptr;   // fused plans: the kernel channel's ids in scatter order
+    uint16_t* inv_perm = nullptr;   //   and each one's position in its sorted piece
     uint8_t* cls = nullptr;         // bank class of each binned point
     float2* samples_b = nullptr;    // A*b weights in scatter order (written by the scatter pass)
     uint16_t* perm = nullptr;       // per payload position: index in scatter order within its piece
@@ -190,6 +192,9 @@ cudaError_t launch_spread_only(Plan& P, int M, bool kernel_channel);    // sprea
 // points of the kernel channel's binning (launch_bin(P, M, true)), the A*b weights read
 // from ws.samples.  FIRM_FLAG_FUSED plans only.
 cudaError_t launch_spread_fused(Plan& P, int M);
+// The fused pass's A*b weights gathered into payload order (ws.samples_b) and each work
+// item's largest |h b| (ws.wmax_item); after the image DFT, before launch_spread_fused.
+cudaError_t launch_fused_gather(Plan& P, int M);
 // One persistent launch spreading the binned points of n plans (same W) into their own
 // fine grids; each plan's grid cleared and its points binned beforehand.  args: device
 // array of n per-plan descriptors; item_off: device (n + 1) ints; queue: device int.

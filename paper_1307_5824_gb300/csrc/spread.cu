@@ -401,9 +401,14 @@ constexpr int kSortSmem = kChunk * (4 + 1) + kSortLevels * (4 + 4);   // ids, cl
 // in perm at its new position: the A*b weights stay where the scatter put them (in
 // scatter order, samples_b), and the spreading pass reads them through perm from
 // within the piece's own 64 KB window instead of one scattered sector per point.
+// With in != nullptr the ids are read from `in` (scatter order, kept) and written sorted
+// to payload; inv_perm != nullptr receives, at each point's scatter position, its
+// position in the sorted piece (the fused form's weight gather walks the points in
+// scatter order, where the points of one image sit together).
 __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ payload, const uint8_t* __restrict__ cls,
                                                     const int4* __restrict__ work, const int* __restrict__ counters,
-                                                    uint16_t* __restrict__ perm) {
+                                                    uint16_t* __restrict__ perm, const uint32_t* __restrict__ in,
+                                                    uint16_t* __restrict__ inv_perm) {
     extern __shared__ uint32_t sm_u[];
     uint32_t* s_ids = sm_u;                                         // kChunk
     uint32_t* s_mask = s_ids + kChunk;                              // kSortLevels: classes with n_c > r
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ paylo
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int i = i0 + u * blockDim.x;
-                if (i < len) { c[u] = cls[wk.y + i]; id[u] = payload[wk.y + i]; }
+                if (i < len) { c[u] = cls[wk.y + i]; id[u] = in ? in[wk.y + i] : payload[wk.y + i]; }
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -491,6 +496,7 @@ __global__ void __launch_bounds__(256) k_class_sort(uint32_t* __restrict__ paylo
             }
             payload[wk.y + pos] = s_ids[i];
             if (perm) perm[wk.y + pos] = (uint16_t)i;
+            if (inv_perm) inv_perm[wk.y + i] = (uint16_t)pos;
         }
         __syncthreads();
     }
@@ -511,8 +517,10 @@ static void bin_w(Plan& P, const BinArgs& a0, int nbricks, bool kc) {
     if (kc) k_bin_scatter2d<W, true><<<grid2, 256, 0, P.stream>>>(a, M, hN, w.colinfo, tiles_x, n_tiles);
     else k_bin_scatter2d<W, false><<<grid2, 256, 0, P.stream>>>(a, M, hN, w.colinfo, tiles_x, n_tiles);
     cudaFuncSetAttribute(k_class_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+    const bool keep = kc && w.payload_scat;       // fused plans keep the scatter order
     k_class_sort<<<P.num_sms * 4, 256, kSortSmem, P.stream>>>(w.payload, w.cls, w.work, w.counters,
-                                                               kc ? nullptr : w.perm);
+                                                               kc ? nullptr : w.perm, keep ? w.payload_scat : nullptr,
+                                                               keep ? w.inv_perm : nullptr);
 }
 
 cudaError_t launch_bin(Plan& P, int M, bool kc) {
@@ -526,7 +534,7 @@ cudaError_t launch_bin(Plan& P, int M, bool kc) {
     a.geom = w.geom;
     a.htab = w.htab;
     a.count = w.count;
-    a.payload = w.payload;
+    a.payload = kc && w.payload_scat ? w.payload_scat : w.payload;
     a.cls = w.cls;
     a.samples = kc ? nullptr : w.samples;
     a.samples_b = w.samples_b;
@@ -1015,7 +1023,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_spread_fused(const SpreadArgs
 // The fused pass's A*b weights in payload order (samples_b[pos] = h b of the point at
 // pos, one gathered 8-byte read per point) and each work item's largest |h b| (its
 // fixed-point scale), so the spreading pass reads both coalesced.
-__global__ void __launch_bounds__(256) k_fused_gather(const uint32_t* __restrict__ payload,
+__global__ void __launch_bounds__(256) k_fused_gather(const uint32_t* __restrict__ scat,
+                                                      const uint16_t* __restrict__ inv_perm,
                                                       const int4* __restrict__ work, const int* __restrict__ counters,
                                                       const float2* __restrict__ samples, int nH,
                                                       float2* __restrict__ samples_b, float* __restrict__ wmax_item) {
@@ -1025,10 +1034,12 @@ __global__ void __launch_bounds__(256) k_fused_gather(const uint32_t* __restrict
     for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
         const int4 wk = work[item];
         float wmax = 0.0f;
+        // the points in scatter order (an image's points of this brick together: their
+        // weights share sectors), each written to its sorted position
         for (int i = threadIdx.x; i < wk.z; i += blockDim.x) {
-            const uint32_t id = __ldg(&payload[wk.y + i]);
+            const uint32_t id = __ldg(&scat[wk.y + i]);
             const float2 v = __ldg(&samples[(size_t)(id >> kTBits) * nH + (id & ((1u << kTBits) - 1u))]);
-            samples_b[wk.y + i] = v;
+            samples_b[wk.y + __ldg(&inv_perm[wk.y + i])] = v;
             wmax = fmaxf(wmax, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
 #pragma unroll
@@ -1144,15 +1155,21 @@ cudaError_t launch_spread(Plan& P, int M, bool kc) {
     return launch_spread_only(P, M, kc);
 }
 
+cudaError_t launch_fused_gather(Plan& P, int M) {
+    if (M <= 0) return cudaSuccess;
+    Workspace& w = P.ws;
+    if (!w.payload_scat) return cudaErrorInvalidValue;      // fused plans only
+    k_fused_gather<<<P.num_sms * 8, 256, 0, P.stream>>>(w.payload_scat, w.inv_perm, w.work, w.counters, w.samples,
+                                                       P.nH, w.samples_b, w.wmax_item);
+    P.launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spread_fused(Plan& P, int M) {
     const size_t cells = (size_t)P.Gk * P.Gk * P.Gk;
     cudaError_t e = cudaMemsetAsync(P.ws.grid, 0, sizeof(double) * 3 * cells, P.stream);
     if (e != cudaSuccess || M <= 0) return e;
     SpreadArgs a = spread_args(P, true);
-    k_fused_gather<<<P.num_sms * 8, 256, 0, P.stream>>>(a.payload, a.work, a.counters, P.ws.samples, P.nH,
-                                                       P.ws.samples_b, P.ws.wmax_item);
-    P.launches += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     a.samples_b = P.ws.samples_b;
     a.wmax_item = P.ws.wmax_item;
     switch (P.p.W) {
