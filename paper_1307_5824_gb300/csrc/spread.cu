@@ -851,13 +851,14 @@ __global__ void k_batch_items(const SpreadArgs* __restrict__ desc, int n, int* _
 // Both channels in one pass (the fused form of FIRM steps 2-3): the points of the
 // kernel channel's binning on the 4N grid (which needs the poses only, so it can run
 // while the images are still uploading) carry both weights, h^2 (eq. kernel) and h b
-// (eq. backprojection, read from the image DFT's [m][t] samples by point id), and every
-// window tap is formed once and added to three shared-memory planes (Ker; A*b real and
-// imaginary).  Level 2 goes to the FP64 Ker
+// (eq. backprojection: the image DFT's [m][t] samples, put in the binning's order by
+// k_fused_gather), and every window tap is formed once and added to three shared-memory
+// planes (Ker; A*b real and imaginary).  Level 2 goes to the FP64 Ker
 // grid (real, G^3) and the FP64 A*b grid (complex, G^3, right after it); A*b is then
 // read from the 4N grid (oversampling 4 for its N modes).  Fixed point as in
 // spread_piece: the kernel channel's scale comes from the largest h^2 of the CTF table,
-// the A*b scale from the piece's own largest |h b|; PPR points per thread between folds.
+// the A*b scale from the piece's own largest |h b| (recorded by the gather); PPR points
+// per thread between folds.
 // ---------------------------------------------------------------------------
 // T threads per block (256; the three planes take 66 KB at W = 6, three blocks per SM:
 // 512-thread blocks, twice the warps per SM, measured 10% slower); with PPR points per
