@@ -148,7 +148,7 @@ def test_cg_config1_matches_oracle(F, W):
     FP32 moves it by ~8e-5, test_c1_fp32_fft_drift; the FP64 CG mode, on the same FP32
     Ker and A*b, lands at 7e-6), and which way depends on the rounding.  Measured 5e-5 to
     2e-4 at W = 6 and 7 over such rounding-level changes, so the FP32 gate is 3e-4; the
-    the benchmark spec's 1e-4 is met by the FP64 CG mode at both widths
+    volume target of 1e-4 is met by the FP64 CG mode at both widths
     (test_cg_config1_fp64_mode_matches_oracle)."""
     tol = 3e-4
     inp = synth.config_inputs("C1")
