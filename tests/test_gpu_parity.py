@@ -190,8 +190,8 @@ def test_cg_config1_matches_oracle(F, W):
 @pytest.mark.parametrize("W", [6, 7])
 def test_cg_config1_fp64_mode_matches_oracle(F, W):
     """The N=32 workload's 10 CG iterations (lambda=0) in the FP64 CG mode: FP64 vectors,
-    FP64 K-hat and Toeplitz apply, Ker and A*b from the FP32 NUFFT.  Gate 1e-4 (north
-    star) at the workload's own W=6 and at W=7."""
+    FP64 K-hat and Toeplitz apply, Ker and A*b from the FP32 NUFFT.  Gate 1e-4 (the
+    volume target) at the workload's own W=6 and at W=7."""
     inp = synth.config_inputs("C1")
     N, M = inp["N"], inp["M"]
     K, h = _oracle_h(inp)
