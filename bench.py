@@ -176,6 +176,17 @@ def workload_name(inp, W, precond, name):
             % (N, M, N, N, c["n_blobs"], views, groups, c["snr"], W, precond))
 
 
+def run_config(inp, args):
+    """The `config` object of the benchmark line: the same for this arm and the
+    reference arm (the oracle), which reconstructs the same workload."""
+    N, M = inp["N"], inp["M"]
+    fused = args.channels == "fused"
+    return {"workload": workload_name(inp, args.W, args.precond, args.workload), "N": N, "M": M, "W": args.W,
+            "precond": args.precond, "channels": args.channels,
+            "l2": "inputs larger than L2: %.2f GB BF16 images read and %.2f GB of FP64 fine grids written every "
+                  "step" % (M * N * N * 2 / 1e9, (3 if fused else 1) * (4 * N) ** 3 * 8 / 1e9)}
+
+
 def disc_size(N):
     h = N // 2
     k = np.arange(-h, h + 1)
@@ -355,8 +366,9 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/recon", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(1, args.steps) * 1e3,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(inp, args.W, "none", name),
-                      "N": inp["N"], "M": inp["M"], "W": 6, "precond": "none (the oracle's plain CG)"},
+           # the workload this arm reconstructs is the GPU arm's (its line carries the same
+           # config); how the oracle reconstructs it (plain CG, FP64) is in cpu_baseline.sample
+           "config": run_config(inp, args),
            "cpu_baseline": {"value": v, "unit": "s/recon", "cores": cores_used(), "kind": "oracle",
                             "sample": sample, "cpu_model": host_cpu_model(), "parts_fixed": fixed},
            "e2e": {"value": v, "unit": "s/recon", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -928,12 +940,7 @@ def main():
         "metric": METRIC, "value": ms_per_recon / 1e3, "unit": "s/recon", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(inp, W, args.precond, args.workload),
-                   "N": N, "M": M, "W": W, "precond": args.precond,
-                   "channels": args.channels,
-                   "l2": "inputs larger than L2: %.2f GB BF16 images read and %.2f GB of FP64 fine grids "
-                         "written every step" % (M * N * N * 2 / 1e9,
-                                                 (3 if fused else 1) * (4 * N) ** 3 * 8 / 1e9)},
+        "config": run_config(inp, args),
         "channels": args.channels,
         "spread_gpts_per_s": pts / (spread_ms * 1e-3) / 1e9,
         "spread_points": pts,
