@@ -86,7 +86,8 @@ typedef struct {
 
 typedef struct {
     int N;            /* volume edge: 16, 32, 48, 64, 80, 96 or 128 */
-    int M;            /* largest image count any call on the plan will pass */
+    int M;            /* largest image count any call on the plan will pass; M < 2^19 and
+                         M * (|K| + 1) / 2 < 2^31 (|K| = the disc size), else FIRM_EINVAL */
     int n_groups;     /* defocus groups in the CTF table; 0 means no CTF (h = 1) */
     int W;            /* Kaiser-Bessel window width in fine-grid cells: 6, 7 or 8 */
     double sigma;     /* NUFFT oversampling; only 2 is supported */

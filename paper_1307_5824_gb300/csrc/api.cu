@@ -251,6 +251,8 @@ static int check_params(const firm_params* p) {
     if (!(p->lambda >= 0.0)) return FIRM_EINVAL;
     // point ids are m << 13 | t: t < 8192 and m < 2^19
     if ((disc_size(p->N) + 1) / 2 >= (1 << kTBits) || p->M >= (1 << (32 - kTBits))) return FIRM_EINVAL;
+    // positions in the binned id array (work items, cursors) are 32-bit signed
+    if ((long long)p->M * ((disc_size(p->N) + 1) / 2) >= (1ll << 31)) return FIRM_EINVAL;
     return FIRM_OK;
 }
 

@@ -40,8 +40,12 @@ def test_workspace_size_and_argument_checks(lib):
     assert L.firm_workspace_size(p64) > small
     with pytest.raises(L.FirmError):
         L.firm_workspace_size(L.make_params(128, 10, 0, 6, flags=L.FIRM_FLAG_FP64_CG))
+    # positions in the binned point array are 32-bit: at N=128 (6,427 half-disc samples
+    # per image) 334,000 images fit, 335,000 do not; image ids take 19 bits
+    assert L.firm_workspace_size(L.make_params(128, 334000, 1, 6)) > big
     for bad in (L.make_params(30, 10), L.make_params(32, 10, W=5), L.make_params(32, 10, sigma=1.5),
-                L.make_params(32, 10, disc_mode=1), L.make_params(32, -1)):
+                L.make_params(32, 10, disc_mode=1), L.make_params(32, -1), L.make_params(128, 335000, 1, 6),
+                L.make_params(16, 1 << 19)):
         with pytest.raises(L.FirmError) as e:
             L.firm_workspace_size(bad)
         assert e.value.code == L.FIRM_EINVAL
