@@ -59,7 +59,7 @@ TRAIN_DEFAULTS = {"C3": (3000, 96, 10000), "C5": (2000, 64, 3000), "RCT": (3000,
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="firm", choices=["firm", "reference"])
     ap.add_argument("--images", type=int, default=None, help="override image count (smaller runs)")
