@@ -153,8 +153,9 @@ int firm_backproject(firm_plan_t plan, int M, const void* images, const double* 
  * Both sums run over the same slice points xi_{m,k} with the same window, so the
  * points are binned once on the 4N^3 grid (poses only: this runs while a staged image
  * upload, firm_stage_images, is still landing), the images are transformed to h b on
- * the disc, and one spreading pass adds h^2 phi to the Ker grid and h b phi to the A*b
- * grid (complex, 4N^3); Ker (on [-N, N)^3), K-hat, lam_eff and A*b (on N^3, from the
+ * the disc, the h b of every point is gathered into the binning's order, and one
+ * spreading pass adds h^2 phi to the Ker grid and h b phi to the A*b grid (complex,
+ * 4N^3); Ker (on [-N, N)^3), K-hat, lam_eff and A*b (on N^3, from the
  * 4N grid: oversampling 4 for its N modes) follow as in firm_kernel and
  * firm_backproject, whose results it replaces.  Arguments as those two calls;
  * khat_out and rhs_out are nullable.  FIRM_EINVAL unless the plan was made with
